@@ -1,0 +1,210 @@
+"""FP64 CPU oracle for Radiant Foam ray tracing (arXiv 2502.01157).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg may import this package.  The CUDA
+renderer does not use it, and the two share no code.
+
+The arithmetic lives in ``rf_oracle.c`` (plain C, FP64, OpenMP over rays); this
+module compiles it with gcc on first use and marshals numpy arrays.  Every
+function follows the paper's statement of the method:
+
+* :func:`camera_rays`  -- pinhole rays through pixel centres (the inputs o, d
+  of Alg. 1).
+* :func:`nearest_site` -- nn(o), the initial cell of Alg. 1.
+* :func:`render`       -- Alg. 1 with Eq. (2)-(3) compositing (Sec. 3.1-3.2).
+* :func:`render_bwd`   -- reverse-mode gradient of the rendered outputs; sites
+  receive gradient only through segment widths (Sec. 3.1).
+* :func:`sh_basis`     -- real spherical harmonics of degree <= 3 (Sec. 3.4).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "librf_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+RAY_OK = 0
+RAY_MAX_STEPS = 1
+
+_d = ctypes.POINTER(ctypes.c_double)
+_i64 = ctypes.POINTER(ctypes.c_int64)
+_i32 = ctypes.POINTER(ctypes.c_int32)
+_u8 = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile rf_oracle.c into a shared library (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+    if r.returncode != 0:  # no OpenMP runtime: build serial
+        r = subprocess.run(base, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_sh_basis_batch.argtypes = [ctypes.c_int, ctypes.c_int64, _d, _d]
+            L.orc_sh_basis_batch.restype = ctypes.c_int
+            L.orc_camera_ray.argtypes = [_d, ctypes.c_int64, _d, _d]
+            L.orc_camera_ray.restype = None
+            L.orc_nearest_site.argtypes = [ctypes.c_int64, _d, _d, _d]
+            L.orc_nearest_site.restype = ctypes.c_int64
+            L.orc_render.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int, _d,
+                                     _d, ctypes.c_int64, _i64, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_double, _d, _d, _d, _i32, _u8, _u8, ctypes.c_int,
+                                     _i32, _d, ctypes.c_int]
+            L.orc_render.restype = ctypes.c_int
+            L.orc_render_bwd.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int, _d,
+                                         _d, ctypes.c_int64, _i64, ctypes.c_double, ctypes.c_int,
+                                         _d, _d, _d, _d, _d, _d, ctypes.c_int]
+            L.orc_render_bwd.restype = ctypes.c_int
+            L.orc_num_threads.argtypes = []
+            L.orc_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _cam(cam) -> np.ndarray:
+    return _f64(cam.as_f64() if hasattr(cam, "as_f64") else cam)
+
+
+def default_tau(scene, cam) -> float:
+    """Degeneracy distance: 1e-6 in units of the scene's coordinate magnitude
+    (at least 1), i.e. a fixed number of FP32 ulps of the coordinates."""
+    c = _cam(cam)
+    mag = max(1.0, float(np.max(np.abs(scene.aabb_min))), float(np.max(np.abs(scene.aabb_max))),
+              float(np.max(np.abs(c[[3, 7, 11]]))))
+    return 1e-6 * mag
+
+
+class _SceneF64:
+    def __init__(self, scene):
+        self.n = int(len(scene.pos))
+        self.pos = _f64(scene.pos).reshape(-1)
+        self.off = np.ascontiguousarray(scene.adj_off, dtype=np.int64)
+        self.adj = np.ascontiguousarray(scene.adj_idx, dtype=np.int32)
+        self.sigma = _f64(scene.density).reshape(-1)
+        self.sh = _f64(scene.sh).reshape(-1)
+        self.deg = int(scene.sh_degree)
+        self.box = _f64(np.concatenate([np.asarray(scene.aabb_min, np.float64).reshape(3),
+                                        np.asarray(scene.aabb_max, np.float64).reshape(3)]))
+
+
+def sh_basis(degree: int, dirs) -> np.ndarray:
+    d = _f64(dirs).reshape(-1, 3)
+    K = (degree + 1) ** 2
+    out = np.zeros((len(d), K))
+    if lib().orc_sh_basis_batch(int(degree), len(d), _p(d, _d), _p(out, _d)):
+        raise ValueError("degree must be 0..3")
+    return out
+
+
+def camera_rays(cam, pixels=None):
+    c = _cam(cam)
+    n = int(c[16]) * int(c[17])
+    px = np.arange(n, dtype=np.int64) if pixels is None else np.asarray(pixels, np.int64)
+    o = np.zeros((len(px), 3))
+    d = np.zeros((len(px), 3))
+    L = lib()
+    for k, p in enumerate(px):
+        L.orc_camera_ray(_p(c, _d), int(p), _p(o[k], _d), _p(d[k], _d))
+    return o, d
+
+
+def nearest_site(pos, q):
+    P = _f64(pos).reshape(-1)
+    Q = _f64(q).reshape(3)
+    gap = np.zeros(1)
+    i = lib().orc_nearest_site(len(P) // 3, _p(P, _d), _p(Q, _d), _p(gap, _d))
+    return int(i), float(gap[0])
+
+
+def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
+           tau=None, trace: int = 0, threads: int = 0) -> dict:
+    """Forward render (Alg. 1, Eq. 2).  Returns rgb [R,3], trans [R], depth [R],
+    steps [R], status [R], degen [R] and, if ``trace > 0``, trace_cells
+    [R,trace] (-1 padded) and trace_t [R,trace]."""
+    S = _SceneF64(scene)
+    c = _cam(cam)
+    n_all = int(c[16]) * int(c[17])
+    px = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
+    R = n_all if px is None else len(px)
+    tau = default_tau(scene, cam) if tau is None else float(tau)
+    rgb = np.zeros((R, 3))
+    tr = np.zeros(R)
+    dp = np.zeros(R)
+    st = np.zeros(R, np.int32)
+    ss = np.zeros(R, np.uint8)
+    dg = np.zeros(R, np.uint8)
+    tc = np.full((R, max(trace, 1)), -1, np.int32)
+    tt = np.full((R, max(trace, 1)), np.nan)
+    rc = lib().orc_render(S.n, _p(S.pos, _d), _p(S.off, _i64), _p(S.adj, _i32), _p(S.sigma, _d),
+                          _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d), R, _p(px, _i64),
+                          float(eps), int(max_steps), tau, _p(rgb, _d), _p(tr, _d), _p(dp, _d),
+                          _p(st, _i32), _p(ss, _u8), _p(dg, _u8), int(trace), _p(tc, _i32),
+                          _p(tt, _d), int(threads))
+    if rc:
+        raise ValueError("oracle render: bad arguments")
+    out = dict(rgb=rgb, trans=tr, depth=dp, steps=st, status=ss, degen=dg.astype(bool), tau=tau)
+    if trace > 0:
+        out["trace_cells"] = tc
+        out["trace_t"] = tt
+    return out
+
+
+def render_bwd(scene, cam, g_rgb, g_trans=None, g_depth=None, pixels=None, eps: float = 1e-4,
+               max_steps: int = 1 << 16, threads: int = 0) -> dict:
+    """Gradient of sum(g_rgb*rgb) + sum(g_trans*trans) + sum(g_depth*depth)
+    with respect to density [N], SH [N,K,3] and positions [N,3]."""
+    S = _SceneF64(scene)
+    c = _cam(cam)
+    n_all = int(c[16]) * int(c[17])
+    px = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
+    R = n_all if px is None else len(px)
+    gr = _f64(g_rgb).reshape(R, 3)
+    gt = None if g_trans is None else _f64(g_trans).reshape(R)
+    gd = None if g_depth is None else _f64(g_depth).reshape(R)
+    K = (S.deg + 1) ** 2
+    g_sigma = np.zeros(S.n)
+    g_sh = np.zeros((S.n, K, 3))
+    g_pos = np.zeros((S.n, 3))
+    rc = lib().orc_render_bwd(S.n, _p(S.pos, _d), _p(S.off, _i64), _p(S.adj, _i32),
+                              _p(S.sigma, _d), _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d), R,
+                              _p(px, _i64), float(eps), int(max_steps), _p(gr, _d), _p(gt, _d),
+                              _p(gd, _d), _p(g_sigma, _d), _p(g_sh, _d), _p(g_pos, _d),
+                              int(threads))
+    if rc:
+        raise ValueError("oracle render_bwd: bad arguments")
+    return dict(density=g_sigma, sh=g_sh, pos=g_pos)

@@ -1,0 +1,489 @@
+/*
+ * rf_oracle.c -- plain, slow FP64 CPU oracle for Radiant Foam ray tracing
+ * (Govindarajan et al., "Radiant Foam: Real-Time Differentiable Ray Tracing",
+ * arXiv 2502.01157).
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline / reference leg load this file.  The CUDA renderer
+ * never calls it and shares no code with it.
+ *
+ * What it computes (all in FP64, one ray at a time, in the paper's order):
+ *
+ *   - Ray generation for a pinhole camera (pixel centres, OpenCV frame).
+ *   - The initial cell nn(o): the site nearest to the ray origin (Alg. 1).
+ *   - The walk of Alg. 1 (Sec. 3.2): in cell i, over every neighbour j in
+ *     N(i), intersect the ray with the bisector plane of x_i and x_j; a plane
+ *     whose normal x_j - x_i makes an angle below 90 deg with d is an exit
+ *     (Fig. 3); the nearest exit (strict <, first in adjacency order on ties)
+ *     gives t_1 and the next cell.
+ *   - Piecewise-constant compositing, Eq. (2)-(3): alpha = 1 - exp(-sigma
+ *     delta), C += T alpha c, T *= (1 - alpha), while T > eps.
+ *   - Colour from real spherical harmonics of degree <= 3 in the ray
+ *     direction, plus 0.5, clamped at 0 (Sec. 3.4 "Training").
+ *   - The gradient of (rgb, transmittance, depth) with respect to density,
+ *     SH coefficients and site positions, by plain reverse-mode
+ *     differentiation of the stored segment list; positions receive gradient
+ *     only through the segment widths (Sec. 3.1).
+ *
+ * Readings where the paper is silent (shared with the CUDA path only as a
+ * specification, not as code):
+ *   - every ray is clipped to [t_min, t_max] = [max(t_near, box entry),
+ *     min(t_far, box exit)] of the scene box; a ray that misses the box returns
+ *     rgb 0, T 1, depth 0;
+ *   - the walk starts at t_0 = 0 in nn(o); segments are composited over their
+ *     part inside [t_min, t_max]; it stops when T <= eps (checked before each
+ *     step), when the exit lies at or beyond t_max, or when the cell has no
+ *     exit (an unbounded hull cell);
+ *   - t_0 <- max(t_0, t_1) (equal to t_0 <- t_1 in exact arithmetic);
+ *   - depth = sum_n T_n alpha_n (a_n + b_n) / 2, the weighted midpoint of the
+ *     composited part [a_n, b_n] of each segment.
+ *
+ * Near-degenerate rays: a ray is flagged when (a) some step's end point lies
+ * within tau of the plane of another face of the same cell, (b) the camera
+ * lies within tau of the bisector of its two nearest sites, or (c) the
+ * transmittance is within a relative 1e-3 of eps at a stop test.  On such rays
+ * a correct FP32 renderer may visit a different cell sequence.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_RAY_OK 0
+#define ORC_RAY_MAX_STEPS 1
+
+/* ------------------------------------------------------------------------ */
+/* Real spherical harmonics (orthonormal on the unit sphere, no Condon-      */
+/* Shortley phase), index l*l + l + m, written out in Cartesian form from    */
+/* Y_l^m = sqrt(2) N_l^|m| P_l^|m|(cos th) {cos(m phi), sin(|m| phi)}.        */
+/* ------------------------------------------------------------------------ */
+int orc_sh_basis(int degree, const double *d, double *Y)
+{
+    const double pi = 3.14159265358979323846;
+    const double x = d[0], y = d[1], z = d[2];
+    if (degree < 0 || degree > 3) return -1;
+    Y[0] = 0.5 * sqrt(1.0 / pi);
+    if (degree >= 1) {
+        const double c1 = sqrt(3.0 / (4.0 * pi));
+        Y[1] = c1 * y;
+        Y[2] = c1 * z;
+        Y[3] = c1 * x;
+    }
+    if (degree >= 2) {
+        const double a = 0.5 * sqrt(15.0 / pi);
+        Y[4] = a * x * y;
+        Y[5] = a * y * z;
+        Y[6] = 0.25 * sqrt(5.0 / pi) * (3.0 * z * z - 1.0);
+        Y[7] = a * x * z;
+        Y[8] = 0.25 * sqrt(15.0 / pi) * (x * x - y * y);
+    }
+    if (degree >= 3) {
+        const double b = 0.25 * sqrt(35.0 / (2.0 * pi));
+        const double c = 0.25 * sqrt(21.0 / (2.0 * pi));
+        Y[9] = b * y * (3.0 * x * x - y * y);
+        Y[10] = 0.5 * sqrt(105.0 / pi) * x * y * z;
+        Y[11] = c * y * (5.0 * z * z - 1.0);
+        Y[12] = 0.25 * sqrt(7.0 / pi) * (5.0 * z * z * z - 3.0 * z);
+        Y[13] = c * x * (5.0 * z * z - 1.0);
+        Y[14] = 0.25 * sqrt(105.0 / pi) * z * (x * x - y * y);
+        Y[15] = b * x * (x * x - 3.0 * y * y);
+    }
+    return 0;
+}
+
+int orc_sh_basis_batch(int degree, int64_t n, const double *dirs, double *Y)
+{
+    const int K = (degree + 1) * (degree + 1);
+    for (int64_t r = 0; r < n; ++r)
+        if (orc_sh_basis(degree, dirs + 3 * r, Y + K * r)) return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Camera: cam[0..11] = c2w (3x4 row-major [R|t]), cam[12..15] = fx fy cx cy, */
+/* cam[16..17] = width height, cam[18..19] = t_near t_far.                    */
+/* Pixel p = v * width + u; its ray passes through the pixel centre.          */
+/* ------------------------------------------------------------------------ */
+void orc_camera_ray(const double *cam, int64_t pixel, double *o, double *d)
+{
+    const int64_t W = (int64_t)cam[16];
+    const int64_t u = pixel % W, v = pixel / W;
+    const double xc = ((double)u + 0.5 - cam[14]) / cam[12];
+    const double yc = ((double)v + 0.5 - cam[15]) / cam[13];
+    const double zc = 1.0;
+    double w[3];
+    for (int r = 0; r < 3; ++r) {
+        w[r] = cam[4 * r + 0] * xc + cam[4 * r + 1] * yc + cam[4 * r + 2] * zc;
+        o[r] = cam[4 * r + 3];
+    }
+    const double len = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    for (int r = 0; r < 3; ++r) d[r] = w[r] / len;
+}
+
+/* Nearest site (lowest index on exact ties); *gap receives the distance from
+ * q to the bisector plane of its two nearest sites (HUGE_VAL if N < 2). */
+int64_t orc_nearest_site(int64_t n, const double *pos, const double *q, double *gap)
+{
+    int64_t b0 = -1, b1 = -1;
+    double d0 = HUGE_VAL, d1 = HUGE_VAL;
+    for (int64_t i = 0; i < n; ++i) {
+        const double dx = pos[3 * i] - q[0], dy = pos[3 * i + 1] - q[1], dz = pos[3 * i + 2] - q[2];
+        const double dd = dx * dx + dy * dy + dz * dz;
+        if (dd < d0) { d1 = d0; b1 = b0; d0 = dd; b0 = i; }
+        else if (dd < d1) { d1 = dd; b1 = i; }
+    }
+    if (gap) {
+        if (b1 < 0) *gap = HUGE_VAL;
+        else {
+            double s = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double t = pos[3 * b1 + a] - pos[3 * b0 + a];
+                s += t * t;
+            }
+            *gap = (d1 - d0) / (2.0 * sqrt(s));
+        }
+    }
+    return b0;
+}
+
+/* Ray / scene-box slab test intersected with [t_near, t_far]. */
+static int ray_interval(const double *o, const double *d, const double *box,
+                        double t_near, double t_far, double *tmin, double *tmax)
+{
+    double lo = t_near > 0.0 ? t_near : 0.0;
+    double hi = t_far > 0.0 ? t_far : HUGE_VAL;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0) {
+            double t1 = (box[a] - o[a]) / d[a];
+            double t2 = (box[3 + a] - o[a]) / d[a];
+            if (t1 > t2) { double s = t1; t1 = t2; t2 = s; }
+            if (t1 > lo) lo = t1;
+            if (t2 < hi) hi = t2;
+        } else if (o[a] < box[a] || o[a] > box[3 + a]) {
+            return 0;
+        }
+    }
+    *tmin = lo;
+    *tmax = hi;
+    return lo < hi;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scene                                                                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;
+    const double *pos;     /* [n,3] */
+    const int64_t *off;    /* [n+1] */
+    const int32_t *adj;    /* [E] */
+    const double *sigma;   /* [n] */
+    const double *sh;      /* [n,K,3] */
+    int deg, K;
+    const double *box;     /* min xyz, max xyz */
+} scene_t;
+
+typedef struct {
+    int64_t cell, next;   /* next = -1: no exit */
+    double t0, t1;        /* raw entry / exit parameters */
+    double a, b;          /* composited part [a,b] (a >= b: nothing) */
+    double delta, sigma, e, T;   /* T: transmittance before the segment */
+    double pre[3], c[3];  /* colour before / after the clamp at 0 */
+} seg_t;
+
+typedef struct {
+    seg_t *s;
+    int64_t n, cap;
+} seglist_t;
+
+static void seg_push(seglist_t *L, const seg_t *s)
+{
+    if (!L) return;
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 256;
+        L->s = (seg_t *)realloc(L->s, (size_t)L->cap * sizeof(seg_t));
+    }
+    L->s[L->n++] = *s;
+}
+
+/* Colour of cell i for the basis values Y (Sec. 3.4: SH of degree <= 3). */
+static void cell_colour(const scene_t *S, int64_t i, const double *Y, double *pre, double *c)
+{
+    for (int ch = 0; ch < 3; ++ch) {
+        double acc = 0.0;
+        for (int k = 0; k < S->K; ++k) acc += S->sh[(i * S->K + k) * 3 + ch] * Y[k];
+        pre[ch] = acc + 0.5;
+        c[ch] = pre[ch] > 0.0 ? pre[ch] : 0.0;
+    }
+}
+
+/* Distance from p to the bisector plane of sites i and k. */
+static double plane_dist(const scene_t *S, int64_t i, int64_t k, const double *p)
+{
+    double num = 0.0, nn = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double n = S->pos[3 * k + a] - S->pos[3 * i + a];
+        const double m = 0.5 * (S->pos[3 * k + a] + S->pos[3 * i + a]);
+        num += n * (p[a] - m);
+        nn += n * n;
+    }
+    return fabs(num) / sqrt(nn);
+}
+
+typedef struct {
+    double rgb[3], T, depth;
+    int32_t steps;
+    uint8_t status, degen;
+} ray_out_t;
+
+/*
+ * Alg. 1 for one ray.  Segments are appended to L (if non-NULL); the visited
+ * cells and raw exit parameters to trace_cells / trace_t (up to max_trace).
+ */
+static void render_ray(const scene_t *S, int64_t start, const double *o, const double *d,
+                       double tmin, double tmax, double eps, int max_steps, double tau,
+                       const double *Y, ray_out_t *R, seglist_t *L,
+                       int max_trace, int32_t *trace_cells, double *trace_t)
+{
+    double T = 1.0, C[3] = {0.0, 0.0, 0.0}, D = 0.0, t0 = 0.0;
+    int64_t i = start;
+    int steps = 0;
+    R->status = ORC_RAY_OK;
+    while (T > eps) {
+        if (fabs(T - eps) <= 1e-3 * eps) R->degen = 1;
+        if (steps >= max_steps) { R->status = ORC_RAY_MAX_STEPS; break; }
+        const double *x = S->pos + 3 * i;
+        /* nearest front-facing bisector plane (Fig. 3) */
+        double t1 = HUGE_VAL;
+        int64_t nxt = -1;
+        for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
+            const int64_t j = S->adj[f];
+            const double *xp = S->pos + 3 * j;
+            double den = 0.0, num = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double n = xp[a] - x[a];
+                const double m = 0.5 * (xp[a] + x[a]);
+                den += n * d[a];
+                num += n * (m - o[a]);
+            }
+            if (den > 0.0) {
+                const double t = num / den;
+                if (t < t1) { t1 = t; nxt = j; }
+            }
+        }
+        /* degeneracy test at the step's end point */
+        {
+            const double te = (nxt >= 0 && t1 < tmax) ? t1 : tmax;
+            double p[3];
+            for (int a = 0; a < 3; ++a) p[a] = o[a] + te * d[a];
+            for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
+                const int64_t k = S->adj[f];
+                if (k == nxt && te == t1) continue;
+                if (plane_dist(S, i, k, p) < tau) { R->degen = 1; break; }
+            }
+        }
+        seg_t s;
+        s.cell = i;
+        s.next = nxt;
+        s.t0 = t0;
+        s.t1 = t1;
+        s.a = t0 > tmin ? t0 : tmin;
+        s.b = t1 < tmax ? t1 : tmax;
+        s.delta = s.b > s.a ? s.b - s.a : 0.0;
+        s.sigma = S->sigma[i];
+        s.e = exp(-s.sigma * s.delta);
+        s.T = T;
+        cell_colour(S, i, Y, s.pre, s.c);
+        const double alpha = 1.0 - s.e;
+        for (int ch = 0; ch < 3; ++ch) C[ch] += T * alpha * s.c[ch];
+        D += T * alpha * 0.5 * (s.a + s.b);
+        T *= s.e;
+        seg_push(L, &s);
+        if (steps < max_trace) {
+            trace_cells[steps] = (int32_t)i;
+            trace_t[steps] = t1;
+        }
+        ++steps;
+        if (nxt < 0 || t1 >= tmax) break;
+        if (t1 > t0) t0 = t1;
+        i = nxt;
+    }
+    if (T <= eps && fabs(T - eps) <= 1e-3 * eps) R->degen = 1;
+    for (int ch = 0; ch < 3; ++ch) R->rgb[ch] = C[ch];
+    R->T = T;
+    R->depth = D;
+    R->steps = steps;
+}
+
+static int setup_scene(scene_t *S, int64_t n, const double *pos, const int64_t *off,
+                       const int32_t *adj, const double *sigma, const double *sh, int deg,
+                       const double *box)
+{
+    if (deg < 0 || deg > 3 || n < 1) return -1;
+    S->n = n; S->pos = pos; S->off = off; S->adj = adj; S->sigma = sigma; S->sh = sh;
+    S->deg = deg; S->K = (deg + 1) * (deg + 1); S->box = box;
+    return 0;
+}
+
+/*
+ * Forward render of n_rays pixels of one camera (pixels == NULL: all pixels
+ * in order).  Outputs per ray: rgb[3], trans, depth, steps, status, degen.
+ * Optional trace (max_trace > 0): cells visited and raw exit parameters,
+ * row-major [n_rays, max_trace].  Returns 0, or -1 on bad arguments.
+ */
+int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int32_t *adj,
+               const double *sigma, const double *sh, int sh_degree, const double *box,
+               const double *cam, int64_t n_rays, const int64_t *pixels,
+               double eps, int max_steps, double tau,
+               double *rgb, double *trans, double *depth, int32_t *steps, uint8_t *status,
+               uint8_t *degen, int max_trace, int32_t *trace_cells, double *trace_t,
+               int n_threads)
+{
+    scene_t S;
+    if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
+    double o[3], dummy[3];
+    orc_camera_ray(cam, 0, o, dummy);
+    double gap;
+    const int64_t start = orc_nearest_site(n_sites, pos, o, &gap);
+    const int cam_degen = gap < tau;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t r = 0; r < n_rays; ++r) {
+        const int64_t px = pixels ? pixels[r] : r;
+        double ro[3], rd[3], Y[16], tmin, tmax;
+        orc_camera_ray(cam, px, ro, rd);
+        orc_sh_basis(S.deg, rd, Y);
+        ray_out_t R;
+        memset(&R, 0, sizeof R);
+        R.T = 1.0;
+        int32_t *tc = max_trace > 0 ? trace_cells + r * (int64_t)max_trace : NULL;
+        double *tt = max_trace > 0 ? trace_t + r * (int64_t)max_trace : NULL;
+        if (ray_interval(ro, rd, box, cam[18], cam[19], &tmin, &tmax)) {
+            render_ray(&S, start, ro, rd, tmin, tmax, eps, max_steps, tau, Y, &R, NULL,
+                       max_trace, tc, tt);
+        }
+        if (cam_degen) R.degen = 1;
+        for (int ch = 0; ch < 3; ++ch) rgb[3 * r + ch] = R.rgb[ch];
+        trans[r] = R.T;
+        depth[r] = R.depth;
+        if (steps) steps[r] = R.steps;
+        if (status) status[r] = R.status;
+        if (degen) degen[r] = R.degen;
+    }
+    return 0;
+}
+
+#ifdef _OPENMP
+#define ORC_ATOMIC _Pragma("omp atomic")
+#else
+#define ORC_ATOMIC
+#endif
+
+/*
+ * Gradient of L = g_rgb . rgb + g_trans * T + g_depth * depth for n_rays
+ * pixels of one camera, accumulated (+=) into g_sigma [N], g_sh [N,K,3] and
+ * g_pos [N,3].  g_trans / g_depth may be NULL (zero).  The forward walk is
+ * repeated with its segments stored, then differentiated in reverse order.
+ */
+int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const int32_t *adj,
+                   const double *sigma, const double *sh, int sh_degree, const double *box,
+                   const double *cam, int64_t n_rays, const int64_t *pixels,
+                   double eps, int max_steps,
+                   const double *g_rgb, const double *g_trans, const double *g_depth,
+                   double *g_sigma, double *g_sh, double *g_pos, int n_threads)
+{
+    scene_t S;
+    if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
+    double o[3], dummy[3];
+    orc_camera_ray(cam, 0, o, dummy);
+    const int64_t start = orc_nearest_site(n_sites, pos, o, NULL);
+    const int K = S.K;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t r = 0; r < n_rays; ++r) {
+        const int64_t px = pixels ? pixels[r] : r;
+        double ro[3], rd[3], Y[16], tmin, tmax;
+        orc_camera_ray(cam, px, ro, rd);
+        orc_sh_basis(S.deg, rd, Y);
+        if (!ray_interval(ro, rd, box, cam[18], cam[19], &tmin, &tmax)) continue;
+        ray_out_t R;
+        memset(&R, 0, sizeof R);
+        seglist_t L = {NULL, 0, 0};
+        render_ray(&S, start, ro, rd, tmin, tmax, eps, max_steps, -1.0, Y, &R,
+                   &L, 0, NULL, NULL);
+        const double gC[3] = {g_rgb[3 * r], g_rgb[3 * r + 1], g_rgb[3 * r + 2]};
+        const double gT = g_trans ? g_trans[r] : 0.0;
+        const double gD = g_depth ? g_depth[r] : 0.0;
+        double Tbar = gT;       /* adjoint of the transmittance after segment k */
+        double t0bar_next = 0.0;  /* adjoint of t0 of segment k+1 */
+        for (int64_t k = L.n - 1; k >= 0; --k) {
+            const seg_t *s = &L.s[k];
+            const double w = s->T * (1.0 - s->e);
+            const double z = 0.5 * (s->a + s->b);
+            double wbar = gD * z;
+            for (int ch = 0; ch < 3; ++ch) wbar += gC[ch] * s->c[ch];
+            /* T_{k+1} = T_k e_k;  C += T_k (1 - e_k) c_k;  D += T_k (1 - e_k) z_k */
+            const double ebar = Tbar * s->T - wbar * s->T;
+            Tbar = Tbar * s->e + wbar * (1.0 - s->e);
+            const double sigbar = ebar * (-s->delta * s->e);
+            const double dbar = ebar * (-s->sigma * s->e);
+            const double zbar = gD * w;
+            double abar = 0.5 * zbar, bbar = 0.5 * zbar;
+            if (s->b > s->a) { bbar += dbar; abar -= dbar; }
+            double t1bar = (s->t1 < tmax) ? bbar : 0.0;
+            double t0bar = (s->t0 > tmin) ? abar : 0.0;
+            /* t0 of segment k+1 = max(t0_k, t1_k) */
+            if (k + 1 < L.n) {
+                if (s->t1 >= s->t0) t1bar += t0bar_next;
+                else t0bar += t0bar_next;
+            }
+            t0bar_next = t0bar;
+            const int64_t i = s->cell;
+            ORC_ATOMIC
+            g_sigma[i] += sigbar;
+            for (int ch = 0; ch < 3; ++ch) {
+                if (!(s->pre[ch] > 0.0)) continue;
+                const double cbar = gC[ch] * w;
+                for (int kk = 0; kk < K; ++kk) {
+                    ORC_ATOMIC
+                    g_sh[(i * K + kk) * 3 + ch] += cbar * Y[kk];
+                }
+            }
+            /* exit parameter t1 of the bisector plane (i, j): dt/dx_j = (x_j - p)/den,
+             * dt/dx_i = (p - x_i)/den with p = o + t1 d, den = (x_j - x_i).d */
+            if (s->next >= 0 && t1bar != 0.0 && isfinite(s->t1)) {
+                const int64_t j = s->next;
+                double den = 0.0, p[3];
+                for (int a = 0; a < 3; ++a) {
+                    den += (pos[3 * j + a] - pos[3 * i + a]) * rd[a];
+                    p[a] = ro[a] + s->t1 * rd[a];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    const double gj = t1bar * (pos[3 * j + a] - p[a]) / den;
+                    const double gi = t1bar * (p[a] - pos[3 * i + a]) / den;
+                    ORC_ATOMIC
+                    g_pos[3 * j + a] += gj;
+                    ORC_ATOMIC
+                    g_pos[3 * i + a] += gi;
+                }
+            }
+        }
+        free(L.s);
+    }
+    return 0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
