@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of differentiable Voronoi-foam ray tracing on GB300.
+
+One step = forward render + MSE loss gradient + backward (re-walk with
+gradient scatter) of one frame of the workload, all in the library's CUDA
+kernels, with the scene resident in HBM.  The headline value is forward +
+backward throughput in Mrays/s on the 3,000,000-site foam at 1920x1080
+(plain FP32 attributes); forward-only, BF16/FP16 attribute storage and
+serving latency are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank renders its own seeded view of the same scene (weak
+scaling) and the site gradients are summed across ranks with one NCCL
+all-reduce per step.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s fwd & fwd+bwd at 3M cells vs plain FP32; serving p50/p99 latency"
+UNIT = "Mrays/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
+    ap.add_argument("--no-extras", action="store_true", help="skip dtype variants / serving")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    "c3": dict(desc="3M sites uniform in [-1,1]^3, SH deg 3, 1920x1080, camera at origin",
+               sites=3_000_000),
+    "c2": dict(desc="1M sites Gaussian mixture + uniform, SH deg 3, 1280x720", sites=1_000_000),
+    "c1": dict(desc="4096 sites uniform, SH deg 0, 64x64", sites=4096),
+}
+
+
+def rank_camera(workload, rank):
+    """Rank 0 uses the workload's camera; other ranks rotate it about the
+    vertical axis by a seeded angle (their own views of the same scene)."""
+    import numpy as np
+    from paper_2502_01157_gb300 import scenes as S
+
+    cam = S.config_cameras(workload)[0]
+    if rank == 0:
+        return cam
+    a = np.random.default_rng(7000 + rank).uniform(0, 2 * math.pi)
+    R = np.array([[math.cos(a), 0, math.sin(a)], [0, 1, 0], [-math.sin(a), 0, math.cos(a)]])
+    c2w = cam.c2w.astype(np.float64).copy()
+    c2w[:, :3] = R @ c2w[:, :3]
+    return S.Camera(c2w, cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.t_near, cam.t_far)
+
+
+def bytes_per_step(k_bar, deg, attr_bytes):
+    """Algorithmic bytes one cell step reads (no reuse): cell record 16 B,
+    next offset 4 B, K faces x 16 B, density and SH coefficients."""
+    return 16 + 4 + 16 * k_bar + attr_bytes + 3 * (deg + 1) ** 2 * attr_bytes
+
+
+def bwd_extra_bytes_per_step(deg):
+    """Backward: read-modify-write of the FP32 gradients touched per step:
+    density 4 B, SH 12 (deg+1)^2 B, and two site positions (one crossing) 24 B."""
+    return 2 * (4 + 12 * (deg + 1) ** 2 + 24)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.path = tempfile.mktemp(prefix="rf_clocks_", suffix=".csv")
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 8:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        import statistics
+
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+def oracle_step(scene, cam, pixels, target):
+    import numpy as np
+    import oracle
+
+    o = oracle.render(scene, cam, pixels=pixels, tau=0.0)
+    g = 2.0 * (o["rgb"] - target[pixels]) / (3 * len(pixels))
+    oracle.render_bwd(scene, cam, g, pixels=pixels)
+
+
+def cpu_baseline(scene, cam, target, budget_s=12.0):
+    """Oracle fwd+bwd on a growing sample of pixels until ~budget_s of work."""
+    import numpy as np
+    import oracle
+
+    R = cam.n_rays
+    rng = np.random.default_rng(11)
+    n = 2048
+    while True:
+        px = np.sort(rng.choice(R, size=min(n, R), replace=False)).astype(np.int64)
+        t = time.perf_counter()
+        oracle_step(scene, cam, px, target)
+        dt = time.perf_counter() - t
+        if dt >= budget_s or n >= R or n >= (1 << 22):
+            break
+        n = int(n * min(8.0, max(2.0, budget_s / max(dt, 1e-3))))
+    return {"value": len(px) / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle fwd+bwd (MSE loss) on {len(px)} random pixels of the "
+                      f"{cam.width}x{cam.height} view, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2502_01157_gb300 import scenes as S
+
+    scene = S.config_scene(args.workload)
+    cam = rank_camera(args.workload, 0)
+    target = S.random_target(cam.n_rays, 2024)
+    rng = np.random.default_rng(5)
+    sample = 8192 if args.workload != "c1" else cam.n_rays
+    times = []
+    for k in range(args.warmup + args.steps):
+        px = np.sort(rng.choice(cam.n_rays, size=sample, replace=False)).astype(np.int64)
+        t = time.perf_counter()
+        oracle_step(scene, cam, px, target)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t)
+    tot = sum(times)
+    v = sample * len(times) / tot / 1e6
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}",
+                       "rays_per_step": sample, "sampled_from_rays": cam.n_rays},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{sample} random pixels per step of the "
+                                       f"{cam.width}x{cam.height} view, fwd+bwd"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import numpy as np
+    from paper_2502_01157_gb300 import scenes as S
+
+    # scene generation uses a spawn process pool: do it before CUDA starts
+    scene = S.config_scene(args.workload)
+    cam = rank_camera(args.workload, rank)
+    target_np = S.random_target(cam.n_rays, 2024 + rank)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2502_01157_gb300 import rf
+
+    R = cam.n_rays
+    deg = scene.sh_degree
+    foam = rf.Foam.from_scene(scene)
+    target = torch.from_numpy(target_np).to(dev)
+    grads = dict(density=torch.zeros(scene.n_sites, device=dev),
+                 sh=torch.zeros(scene.n_sites, (deg + 1) ** 2, 3, device=dev),
+                 pos=torch.zeros(scene.n_sites, 3, device=dev))
+    out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
+               depth=torch.empty(R, device=dev))
+    loss = torch.zeros(1, device=dev)
+    scale = 1.0 / (3 * R)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(marks=None):
+        if marks is not None:
+            marks[0].record()
+        foam.render([cam], out=out)
+        if marks is not None:
+            marks[1].record()
+        d_rgb, _ = rf.mse_grad(out["rgb"], target, scale, loss)
+        if marks is not None:
+            marks[2].record()
+        foam.backward([cam], out, d_rgb, grads=grads)
+        if marks is not None:
+            marks[3].record()
+        if world > 1:
+            for g in grads.values():
+                dist.all_reduce(g)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # workload facts (outside the timed region)
+    chk = foam.render([cam], steps=True)
+    steps_total = int(chk["steps"].sum().item())
+    k_bar = scene.n_edges / scene.n_sites
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    marks = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    t0, t1 = ev(), ev()
+    barrier()
+    t0.record()
+    for k in range(args.steps):
+        step(marks[k])
+    t1.record()
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    fwd_ms = sum(m[0].elapsed_time(m[1]) for m in marks) / args.steps
+    bwd_ms = sum(m[2].elapsed_time(m[3]) for m in marks) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * R / (ms * 1e-3) / 1e6
+
+    # forward-only throughput
+    fwd_only = None
+    res = {}
+    if not args.no_extras:
+        barrier()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(args.steps):
+            foam.render([cam], out=out)
+        b.record()
+        barrier()
+        fwd_only = R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
+        res["fwd_fp32_mrays_s"] = fwd_only
+        # attribute storage variants (same geometry, own copies of the attributes)
+        for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16)):
+            d2 = torch.from_numpy(scene.density).to(dev, dt)
+            s2 = torch.from_numpy(scene.sh).to(dev, dt)
+            foam.set_attributes(d2, s2)
+            for _ in range(2):
+                step()
+            barrier()
+            a, b, c = ev(), ev(), ev()
+            a.record()
+            for _ in range(args.steps):
+                foam.render([cam], out=out)
+            b.record()
+            for _ in range(args.steps):
+                step()
+            c.record()
+            barrier()
+            res[f"fwd_{name}_mrays_s"] = R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
+            res[f"fwdbwd_{name}_mrays_s"] = R / (b.elapsed_time(c) / args.steps * 1e-3) / 1e6
+        foam.set_attributes(torch.from_numpy(scene.density).to(dev),
+                            torch.from_numpy(scene.sh).to(dev))
+
+    # end to end through the public API with host buffers
+    pin_t = torch.from_numpy(target_np).pin_memory()
+    pin_rgb = torch.empty(R, 3).pin_memory()
+    pin_loss = torch.empty(1).pin_memory()
+    barrier()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        target.copy_(pin_t, non_blocking=True)
+        loss.zero_()
+        step()
+        pin_rgb.copy_(out["rgb"], non_blocking=True)
+        pin_loss.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = (time.perf_counter() - w0) / args.steps
+    barrier()
+
+    # roofline of the dominant kernel (the backward re-walk)
+    attr_b = 4
+    fwd_bytes = bytes_per_step(k_bar, deg, attr_b) * steps_total + 20 * R
+    bwd_bytes = (bytes_per_step(k_bar, deg, attr_b) + bwd_extra_bytes_per_step(deg)) * steps_total + 32 * R
+    import json as _j
+
+    peaks = {}
+    try:
+        peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        peak, peak_src = 6800.0, "fallback"
+    dominant = "bwd" if bwd_ms >= fwd_ms else "fwd"
+    kb = bwd_bytes if dominant == "bwd" else fwd_bytes
+    kms = bwd_ms if dominant == "bwd" else fwd_ms
+    achieved = kb / (kms * 1e-3) / 1e9
+    roof = {"kernel": f"rf::{dominant}_kernel<float,{deg}>", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "bytes_per_cell_step": (bytes_per_step(k_bar, deg, attr_b) +
+                                                     (bwd_extra_bytes_per_step(deg) if dominant == "bwd" else 0)),
+            "cell_steps_per_launch": steps_total, "ms_per_launch": kms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}",
+                       "n_sites": scene.n_sites, "n_edges": scene.n_edges, "rays_per_step": R,
+                       "cell_steps_per_ray": steps_total / R, "sh_degree": deg,
+                       "step": "fwd + mse grad + bwd (FP32 attributes)",
+                       "l2": "inputs larger than L2 (packed foam %.2f GB)" % (foam.info()["device_bytes"] / 1e9),
+                       "parallelism": f"dp{world}" if world > 1 else "single"},
+            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "cell_steps_per_s": steps_total / (ms * 1e-3),
+            **res,
+            "gpu_launches": args.steps * 5,
+            "roofline": roof,
+            "clocks": clk,
+            "e2e": {"value": R / e2e_s / 1e6, "unit": UNIT,
+                    "h2d_bytes_per_step": int(pin_t.numel() * 4),
+                    "d2h_bytes_per_step": int(pin_rgb.numel() * 4 + 4)}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, cam, target_np)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

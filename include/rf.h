@@ -1,0 +1,219 @@
+/*
+ * rf.h -- C ABI of the GB300 (sm_103a) Radiant Foam renderer.
+ *
+ * Differentiable ray tracing through a 3D Voronoi foam (Govindarajan et al.,
+ * "Radiant Foam: Real-Time Differentiable Ray Tracing", arXiv 2502.01157).
+ * The scene is a set of sites p_i (Sec. 3.2, Eq. 4); each Voronoi cell carries
+ * a density sigma_i and spherical-harmonic colour coefficients (Sec. 3.4).
+ * Rays walk cell to cell (Alg. 1) and composite Eq. (2)-(3).
+ *
+ * Conventions for every call:
+ *   - Pointers documented "device" are CUDA device pointers owned by the
+ *     caller; the library never frees them.  "host" pointers are read during
+ *     the call only.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream); outputs are valid once the stream reaches that
+ *     point.  Calls return after enqueueing.
+ *   - Every call returns an rf_status; on failure rf_last_error() gives a
+ *     message (thread-local, valid until the next call on the same thread).
+ *     Invalid arguments are rejected before anything is enqueued.
+ *   - Per-ray anomalies (the step cap was reached) are reported in the
+ *     optional per-ray status output, not as a call failure.
+ *   - Calls that use one rf_scene must be ordered on one stream: the scene
+ *     owns a small device workspace (start cells per camera) that renders
+ *     reuse.
+ */
+#ifndef RF_H
+#define RF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+#define RF_API extern "C" __attribute__((visibility("default")))
+#else
+#define RF_API __attribute__((visibility("default")))
+#endif
+
+#define RF_VERSION 1
+#define RF_MAX_SH_DEGREE 3
+
+typedef enum rf_status {
+    RF_OK = 0,
+    RF_ERR_INVALID_ARG = 1,  /* a pointer, size, dtype or camera is invalid */
+    RF_ERR_CUDA = 2,         /* a CUDA runtime call failed (message has the reason) */
+    RF_ERR_OOM = 3,          /* device allocation failed */
+    RF_ERR_BUSY = 4,         /* serving: request not admitted (memory or slots) */
+    RF_ERR_NOT_READY = 5,    /* serving: request still in flight */
+    RF_ERR_TIMEOUT = 6,      /* a bounded wait ran out */
+    RF_ERR_BAD_SCENE = 7,    /* adjacency / positions failed validation */
+    RF_ERR_NOT_FOUND = 8     /* serving: unknown request id */
+} rf_status;
+
+/* Storage type of the per-cell attributes (density, SH coefficients).
+ * Geometry, plane intersections and compositing are always FP32. */
+typedef enum rf_dtype { RF_F32 = 0, RF_BF16 = 1, RF_F16 = 2 } rf_dtype;
+
+/* Per-ray status codes (optional output). */
+enum { RF_RAY_OK = 0, RF_RAY_MAX_STEPS = 1 };
+
+/*
+ * Scene description (Sec. 3.2: "a learnable point cloud" of Voronoi sites
+ * whose Delaunay adjacency N(i) is maintained alongside; Sec. 3.4: per-cell
+ * density and degree <= 3 SH colour).
+ *
+ *   pos       device float [n_sites][3]   site positions p_i.
+ *   adj_off   device int32 [n_sites+1]    CSR offsets, adj_off[0] = 0,
+ *                                          adj_off[n_sites] = n_edges.
+ *   adj_idx   device int32 [n_edges]      neighbour ids N(i) of each site, in
+ *                                          the order exits are tie-broken
+ *                                          (first wins).  Must be symmetric,
+ *                                          in range, without self loops or
+ *                                          duplicate positions.  A superset of
+ *                                          the Delaunay neighbours renders the
+ *                                          same image; a missing neighbour
+ *                                          does not.
+ *   density   device [n_sites] of attr_dtype          sigma_i >= 0 (after
+ *                                                     the activation).
+ *   sh        device [n_sites][(deg+1)^2][3] of attr_dtype  coefficients,
+ *             real orthonormal SH index l*l+l+m, RGB innermost; the colour is
+ *             max(0, sum_k sh[i][k][c] Y_k(d) + 0.5).
+ *             density and sh are BORROWED: the scene keeps the pointers; the
+ *             caller keeps them alive and may rewrite their contents between
+ *             renders (see rf_scene_set_attributes to swap them).
+ *             Both must be 16-byte aligned.
+ *   aabb_min/max  scene box; every ray is clipped to it.  If min > max on
+ *             any axis the box of the sites is computed on the device.
+ */
+typedef struct rf_scene_desc {
+    int64_t n_sites;
+    int64_t n_edges;
+    const float *pos;
+    const int32_t *adj_off;
+    const int32_t *adj_idx;
+    const void *density;
+    const void *sh;
+    int32_t sh_degree;
+    int32_t attr_dtype;
+    float aabb_min[3];
+    float aabb_max[3];
+} rf_scene_desc;
+
+/*
+ * Pinhole camera (the ray origins o and unit directions d of Alg. 1).
+ *   c2w      row-major 3x4 [R | t]: camera-frame point x -> R x + t; the
+ *            camera frame is OpenCV (+x right, +y down, +z forward); t is the
+ *            centre (every ray's origin o).
+ *   fx, fy, cx, cy  intrinsics in pixels; pixel (u,v) casts the ray through
+ *            its centre (u+0.5, v+0.5), d = normalise(R ((u+.5-cx)/fx,
+ *            (v+.5-cy)/fy, 1)).
+ *   width, height   image size; ray index = v * width + u.
+ *   t_near, t_far   compositing interval along d, intersected with the scene
+ *            box (t_far <= 0: no limit).
+ */
+typedef struct rf_camera {
+    float c2w[12];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float t_near, t_far;
+} rf_camera;
+
+/*
+ *   eps        transmittance threshold: a ray continues while T > eps
+ *              (Alg. 1).  Default when opts == NULL: 1e-4.
+ *   max_steps  cap on cell steps per ray (<= 0: 65536); a capped ray gets
+ *              RF_RAY_MAX_STEPS.
+ *   flags      reserved, 0.
+ */
+typedef struct rf_render_opts {
+    float eps;
+    int32_t max_steps;
+    uint32_t flags;
+    int32_t reserved;
+} rf_render_opts;
+
+typedef struct rf_scene rf_scene;
+
+RF_API int32_t rf_version(void);
+RF_API const char *rf_last_error(void);
+
+/*
+ * Packs the foam for traversal: per site a 16-byte record (position, first
+ * neighbour) and per directed edge (i, j) a 16-byte face record holding the
+ * bisector normal scaled by 2/|p_j - p_i|^2 and j, so each face test of
+ * Alg. 1 is one coalesced 16-byte load.  Validates the adjacency on the
+ * device (range, self loops, symmetry, zero-length edges) and returns
+ * RF_ERR_BAD_SCENE if it fails.  Allocates the packed copy (16 B per edge
+ * plus 20 B per site) with cudaMalloc; synchronises `stream` once.
+ */
+RF_API rf_status rf_scene_create(const rf_scene_desc *desc, void *stream, rf_scene **out);
+
+/* Swaps the borrowed attribute pointers / dtype (same n_sites, sh_degree). */
+RF_API rf_status rf_scene_set_attributes(rf_scene *scene, const void *density, const void *sh,
+                                         int32_t attr_dtype);
+
+/* Re-packs after the sites moved (same adjacency); pos: device [n_sites][3]. */
+RF_API rf_status rf_scene_update_positions(rf_scene *scene, const float *pos, void *stream);
+
+/* Scene facts: counts, the box used (6 floats, may be NULL) and device bytes owned. */
+RF_API rf_status rf_scene_info(const rf_scene *scene, int64_t *n_sites, int64_t *n_edges,
+                               float *aabb6, size_t *device_bytes);
+
+/* Frees the packed copy; waits for the device. */
+RF_API rf_status rf_scene_destroy(rf_scene *scene);
+
+/*
+ * Forward render of n_cams cameras in one launch (Alg. 1 per ray, Eq. 2-3).
+ * Outputs are concatenated camera after camera (ray r of camera c at
+ * sum_{c'<c} W_c' H_c' + r):
+ *   rgb    device float [R][3]   composited colour (black background).
+ *   trans  device float [R]      final transmittance T.
+ *   depth  device float [R]      sum_n T_n alpha_n (a_n + b_n)/2 over the
+ *                                composited part [a_n, b_n] of each segment.
+ *   steps  device int32 [R] or NULL   cells visited.
+ *   ray_status device uint8 [R] or NULL   RF_RAY_*.
+ * cams is a host array.  A ray that misses the scene box gives rgb 0, T 1,
+ * depth 0, steps 0.
+ */
+RF_API rf_status rf_render_fwd(rf_scene *scene, const rf_camera *cams, int32_t n_cams,
+                               const rf_render_opts *opts, float *rgb, float *trans,
+                               float *depth, int32_t *steps, uint8_t *ray_status, void *stream);
+
+/*
+ * Backward of rf_render_fwd: each ray is walked again with bit-identical
+ * arithmetic (no per-segment storage) and the gradient of
+ *   L = sum d_rgb . rgb + sum d_trans * trans + sum d_depth * depth
+ * is ACCUMULATED (+=) into
+ *   g_density device float [n_sites]
+ *   g_sh      device float [n_sites][(deg+1)^2][3]
+ *   g_pos     device float [n_sites][3]   (through the segment widths only,
+ *                                          Sec. 3.1)
+ * rgb / trans / depth are the forward outputs of the same call arguments
+ * (depth may be NULL when d_depth is NULL); d_trans / d_depth may be NULL
+ * (zero).  Any gradient output may be NULL to skip it.
+ */
+RF_API rf_status rf_render_bwd(rf_scene *scene, const rf_camera *cams, int32_t n_cams,
+                               const rf_render_opts *opts, const float *rgb,
+                               const float *trans, const float *depth, const float *d_rgb,
+                               const float *d_trans, const float *d_depth, float *g_density,
+                               float *g_sh, float *g_pos, void *stream);
+
+/*
+ * Debug / parity: the cells each ray of one camera visits, in order.
+ *   cells   device int32 [R][max_per_ray]  (-1 after the last cell)
+ *   counts  device int32 [R]                total cells visited (may exceed
+ *                                           max_per_ray)
+ */
+RF_API rf_status rf_trace_cells(rf_scene *scene, const rf_camera *cam,
+                                const rf_render_opts *opts, int32_t max_per_ray,
+                                int32_t *cells, int32_t *counts, void *stream);
+
+/*
+ * MSE loss helper for a training step (device, n = 3 * rays):
+ *   d_rgb[k] = 2 * scale * (rgb[k] - target[k]);  *loss += scale * sum_k (rgb[k]-target[k])^2
+ * loss is a device float accumulated with atomics (zero it first).
+ */
+RF_API rf_status rf_mse_grad(const float *rgb, const float *target, int64_t n, float scale,
+                             float *d_rgb, float *loss, void *stream);
+
+#endif /* RF_H */

@@ -1,0 +1,53 @@
+// rf_host.h -- host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/rf.h"
+#include "rf_internal.cuh"
+
+struct rf_scene {
+    int64_t n_sites = 0;
+    int64_t n_edges = 0;
+    float4 *cells = nullptr;     // [N]
+    int32_t *off = nullptr;      // [N+1]
+    float4 *faces = nullptr;     // [E]
+    const void *density = nullptr;  // borrowed
+    const void *sh = nullptr;       // borrowed
+    int32_t sh_degree = 0;
+    int32_t attr_dtype = RF_F32;
+    float box[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long *start_keys = nullptr;  // workspace [kMaxCamsPerLaunch]
+    int32_t *flags = nullptr;                  // workspace [4] (validation counters)
+    size_t bytes = 0;
+    int device = 0;
+};
+
+namespace rf {
+
+rf_status fail(rf_status code, const char *fmt, ...);
+rf_status cuda_fail(cudaError_t e, const char *what);
+
+#define RF_CUDA(expr)                                                  \
+    do {                                                               \
+        cudaError_t e_ = (expr);                                       \
+        if (e_ != cudaSuccess) return ::rf::cuda_fail(e_, #expr);      \
+    } while (0)
+
+SceneDev scene_dev(const rf_scene *s);
+rf_status check_camera(const rf_camera &c, int index);
+rf_status check_opts(const rf_render_opts *o, float *eps, int32_t *max_steps);
+
+// Start cells nn(o) of cams[0..n) (n <= kMaxCamsPerLaunch) into keys[0..n).
+rf_status launch_nearest_sites(const rf_scene *s, const rf_camera *cams, int n,
+                               unsigned long long *keys, cudaStream_t st);
+
+// Fill a LaunchCams for cams[first .. first+count); returns the tile count.
+int64_t make_launch_cams(const rf_camera *cams, int first, int count, int64_t ray_begin,
+                         LaunchCams *lc);
+
+}  // namespace rf

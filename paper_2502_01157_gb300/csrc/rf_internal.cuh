@@ -1,0 +1,282 @@
+// rf_internal.cuh -- device-side building blocks of the Radiant Foam renderer
+// (arXiv 2502.01157) for sm_103a.
+//
+// Every piece of arithmetic that decides which cells a ray visits (ray
+// generation, the scene-box clip, the exit-face search of Alg. 1, the segment
+// bounds and the transmittance update) is written with explicit
+// round-to-nearest intrinsics and the library is compiled with -fmad=false, so
+// the compiler cannot contract it differently in the forward and backward
+// kernels: the backward re-walk reproduces the forward walk bit for bit.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rf.h"
+
+namespace rf {
+
+constexpr int kMaxCamsPerLaunch = 16;  // cameras per kernel launch (more: several launches)
+constexpr int kTileW = 16;             // pixels per tile (x)
+constexpr int kTileH = 8;              // pixels per tile (y)
+constexpr int kBlock = kTileW * kTileH;  // one thread per pixel of a tile
+constexpr int kDefaultMaxSteps = 1 << 16;
+
+// ---------------------------------------------------------------------------
+// Packed scene (device memory owned by rf_scene)
+//   cells[i] = {x_i, y_i, z_i, bits(first face index)}
+//   off[i]   = first face of cell i (off[N] = E); count = off[i+1] - off[i]
+//   faces[f] = {u_x, u_y, u_z, bits(j)} for the f-th directed edge (i, j),
+//              u = 2 (p_j - p_i) / |p_j - p_i|^2.
+// With o~ = o - p_i the bisector of (p_i, p_j) is crossed at
+//   t = (1 - u . o~) / (u . d),
+// front-facing (an exit, Fig. 3) iff u . d > 0.
+// ---------------------------------------------------------------------------
+struct SceneDev {
+    const float4 *cells;
+    const int32_t *off;
+    const float4 *faces;
+    const void *density;
+    const void *sh;
+    float box_lo[3];
+    float box_hi[3];
+};
+
+// Cameras of one launch and the tile partition of their images.
+struct LaunchCams {
+    rf_camera cam[kMaxCamsPerLaunch];
+    int32_t tile_begin[kMaxCamsPerLaunch + 1];  // prefix over cameras of tile counts
+    int32_t tiles_x[kMaxCamsPerLaunch];
+    int64_t ray_begin[kMaxCamsPerLaunch];       // output offset of each camera
+    int32_t n_cams;
+    int32_t cam0;                               // index of cam[0] in the start-cell table
+};
+
+struct RenderParams {
+    SceneDev s;
+    LaunchCams lc;
+    const unsigned long long *start_keys;  // [cam0 + c] low 32 bits: start cell
+    float eps;
+    int32_t max_steps;
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+// Map a block to (camera, tile) and a thread to a pixel: warp w of the block
+// covers an 8x4 patch of the 16x8 tile, so the 32 rays of a warp are
+// neighbours on the image and walk through mostly the same cells.
+struct PixelTask {
+    int cam, u, v;
+    bool valid;
+};
+
+__device__ __forceinline__ PixelTask pixel_of_thread(const LaunchCams &lc) {
+    PixelTask t;
+    const int tile = blockIdx.x;
+    int c = 0;
+#pragma unroll 1
+    while (c + 1 < lc.n_cams && lc.tile_begin[c + 1] <= tile) ++c;
+    const int lt = tile - lc.tile_begin[c];
+    const int tx = lt % lc.tiles_x[c];
+    const int ty = lt / lc.tiles_x[c];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    t.cam = c;
+    t.u = tx * kTileW + (w & 1) * 8 + (l & 7);
+    t.v = ty * kTileH + (w >> 1) * 4 + (l >> 3);
+    t.valid = t.u < lc.cam[c].width && t.v < lc.cam[c].height;
+    return t;
+}
+
+// Pinhole ray through the centre of pixel (u, v).
+__device__ __forceinline__ void camera_ray(const rf_camera &c, int u, int v, float3 &o, float3 &d) {
+    const float xc = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), c.cx), c.fx);
+    const float yc = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), c.cy), c.fy);
+    const float wx = __fmaf_rn(c.c2w[0], xc, __fmaf_rn(c.c2w[1], yc, c.c2w[2]));
+    const float wy = __fmaf_rn(c.c2w[4], xc, __fmaf_rn(c.c2w[5], yc, c.c2w[6]));
+    const float wz = __fmaf_rn(c.c2w[8], xc, __fmaf_rn(c.c2w[9], yc, c.c2w[10]));
+    const float len = __fsqrt_rn(__fmaf_rn(wx, wx, __fmaf_rn(wy, wy, __fmul_rn(wz, wz))));
+    d = make_float3(__fdiv_rn(wx, len), __fdiv_rn(wy, len), __fdiv_rn(wz, len));
+    o = make_float3(c.c2w[3], c.c2w[7], c.c2w[11]);
+}
+
+// Clip the ray to [t_near, t_far] and the scene box (slab test).
+__device__ __forceinline__ bool ray_interval(const float3 &o, const float3 &d, const SceneDev &s,
+                                             float t_near, float t_far, float &tmin, float &tmax) {
+    float lo = t_near > 0.f ? t_near : 0.f;
+    float hi = t_far > 0.f ? t_far : __int_as_float(0x7f800000);
+    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] != 0.f) {
+            float t1 = __fdiv_rn(__fsub_rn(s.box_lo[a], oo[a]), dd[a]);
+            float t2 = __fdiv_rn(__fsub_rn(s.box_hi[a], oo[a]), dd[a]);
+            if (t1 > t2) { const float q = t1; t1 = t2; t2 = q; }
+            lo = t1 > lo ? t1 : lo;
+            hi = t2 < hi ? t2 : hi;
+        } else if (oo[a] < s.box_lo[a] || oo[a] > s.box_hi[a]) {
+            return false;
+        }
+    }
+    tmin = lo;
+    tmax = hi;
+    return lo < hi;
+}
+
+// Real orthonormal spherical harmonics of degree <= DEG at the unit
+// direction d (no Condon-Shortley phase), index l*l + l + m.
+template <int DEG>
+__device__ __forceinline__ void sh_basis(const float3 &d, float *Y) {
+    const float x = d.x, y = d.y, z = d.z;
+    Y[0] = 0.28209479177387814f;                      // 1/(2 sqrt(pi))
+    if (DEG >= 1) {
+        const float c1 = 0.4886025119029199f;         // sqrt(3/(4 pi))
+        Y[1] = c1 * y;
+        Y[2] = c1 * z;
+        Y[3] = c1 * x;
+    }
+    if (DEG >= 2) {
+        const float a = 1.0925484305920792f;          // sqrt(15/pi)/2
+        Y[4] = a * x * y;
+        Y[5] = a * y * z;
+        Y[6] = 0.31539156525252005f * (3.f * z * z - 1.f);   // sqrt(5/pi)/4
+        Y[7] = a * x * z;
+        Y[8] = 0.5462742152960396f * (x * x - y * y);        // sqrt(15/pi)/4
+    }
+    if (DEG >= 3) {
+        const float b = 0.5900435899266435f;          // sqrt(35/(2 pi))/4
+        const float c = 0.4570457994644658f;          // sqrt(21/(2 pi))/4
+        Y[9] = b * y * (3.f * x * x - y * y);
+        Y[10] = 2.890611442640554f * x * y * z;       // sqrt(105/pi)/2
+        Y[11] = c * y * (5.f * z * z - 1.f);
+        Y[12] = 0.3731763325901154f * z * (5.f * z * z - 3.f);  // sqrt(7/pi)/4
+        Y[13] = c * x * (5.f * z * z - 1.f);
+        Y[14] = 1.445305721320277f * z * (x * x - y * y);       // sqrt(105/pi)/4
+        Y[15] = b * x * (x * x - 3.f * y * y);
+    }
+}
+
+// Unpack 16 bytes of attribute storage into floats.
+template <typename AT>
+__device__ __forceinline__ void unpack16(const uint4 &q, float *out);
+template <>
+__device__ __forceinline__ void unpack16<float>(const uint4 &q, float *out) {
+    out[0] = __uint_as_float(q.x); out[1] = __uint_as_float(q.y);
+    out[2] = __uint_as_float(q.z); out[3] = __uint_as_float(q.w);
+}
+template <typename H2, typename F>
+__device__ __forceinline__ void unpack_half2x4(const uint4 &q, float *out, F cvt) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        H2 h = *reinterpret_cast<const H2 *>(&w[k]);
+        const float2 f = cvt(h);
+        out[2 * k] = f.x;
+        out[2 * k + 1] = f.y;
+    }
+}
+template <>
+__device__ __forceinline__ void unpack16<__nv_bfloat16>(const uint4 &q, float *out) {
+    unpack_half2x4<__nv_bfloat162>(q, out, [](__nv_bfloat162 h) { return __bfloat1622float2(h); });
+}
+template <>
+__device__ __forceinline__ void unpack16<__half>(const uint4 &q, float *out) {
+    unpack_half2x4<__half2>(q, out, [](__half2 h) { return __half22float2(h); });
+}
+
+// Colour before the clamp: pre[ch] = sum_k sh[i][k][ch] Y_k + 0.5, summed in
+// increasing k (Sec. 3.4).
+template <typename AT, int DEG>
+__device__ __forceinline__ void sh_colour(const AT *__restrict__ sh, int i, const float *Y,
+                                          float *pre) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int NV = 3 * K;
+    float acc[3] = {0.f, 0.f, 0.f};
+    if constexpr ((NV * sizeof(AT)) % 16 == 0) {
+        constexpr int EPV = 16 / sizeof(AT);
+        constexpr int NQ = NV / EPV;
+        const uint4 *row = reinterpret_cast<const uint4 *>(sh + (size_t)i * NV);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float v[EPV];
+            unpack16<AT>(ldg(row + q), v);
+#pragma unroll
+            for (int e = 0; e < EPV; ++e) {
+                const int g = q * EPV + e;
+                acc[g % 3] = __fmaf_rn(v[e], Y[g / 3], acc[g % 3]);
+            }
+        }
+    } else {
+        const AT *row = sh + (size_t)i * NV;
+#pragma unroll
+        for (int g = 0; g < NV; ++g) acc[g % 3] = __fmaf_rn(to_f(ldg(row + g)), Y[g / 3], acc[g % 3]);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) pre[ch] = __fadd_rn(acc[ch], 0.5f);
+}
+
+// Exit face of cell i (Alg. 1 inner loop): the front-facing bisector with the
+// smallest crossing parameter, first in adjacency order on ties.  The
+// comparison t_j < t_best is done by cross-multiplication (both denominators
+// are positive), so no division is needed per face.  Returns j or -1.
+__device__ __forceinline__ int find_exit(const float4 *__restrict__ faces, int begin, int end,
+                                         const float3 &d, const float3 &oc, float &num_best,
+                                         float &den_best) {
+    float nb = 1.f, db = 0.f;
+    int jb = -1;
+#pragma unroll 4
+    for (int f = begin; f < end; ++f) {
+        const float4 r = ldg(faces + f);
+        const float den = __fmaf_rn(r.x, d.x, __fmaf_rn(r.y, d.y, __fmul_rn(r.z, d.z)));
+        const float num = __fmaf_rn(-r.x, oc.x, __fmaf_rn(-r.y, oc.y, __fmaf_rn(-r.z, oc.z, 1.f)));
+        if (den > 0.f && __fmul_rn(num, db) < __fmul_rn(nb, den)) {
+            nb = num;
+            db = den;
+            jb = __float_as_int(r.w);
+        }
+    }
+    num_best = nb;
+    den_best = db;
+    return jb;
+}
+
+// One segment's bounds, width, density and colour (shared by all kernels).
+struct Segment {
+    float t1;      // raw exit parameter (inf: no exit)
+    float a, b;    // composited part
+    float delta;
+    float sigma;
+    float e;       // exp(-sigma delta)
+    float pre[3];  // colour before the clamp
+    int next;
+};
+
+template <typename AT, int DEG>
+__device__ __forceinline__ void cell_step(const SceneDev &s, int i, const float4 &cell,
+                                          const float3 &o, const float3 &d, float t0, float tmin,
+                                          float tmax, const float *Y, Segment &g, float3 &oc) {
+    const int begin = __float_as_int(cell.w);
+    const int end = ldg(s.off + i + 1);
+    oc = make_float3(__fsub_rn(o.x, cell.x), __fsub_rn(o.y, cell.y), __fsub_rn(o.z, cell.z));
+    float nb, db;
+    g.next = find_exit(s.faces, begin, end, d, oc, nb, db);
+    g.t1 = g.next >= 0 ? __fdiv_rn(nb, db) : __int_as_float(0x7f800000);
+    g.a = t0 > tmin ? t0 : tmin;
+    g.b = g.t1 < tmax ? g.t1 : tmax;
+    const float w = __fsub_rn(g.b, g.a);
+    g.delta = w > 0.f ? w : 0.f;
+    g.sigma = to_f(ldg(reinterpret_cast<const AT *>(s.density) + i));
+    g.e = expf(-__fmul_rn(g.sigma, g.delta));
+    sh_colour<AT, DEG>(reinterpret_cast<const AT *>(s.sh), i, Y, g.pre);
+}
+
+}  // namespace rf

@@ -1,0 +1,371 @@
+"""Python binding of the C-ABI renderer ``librf.so`` (argument marshalling only).
+
+Every step of the ray-tracing path runs in the library's CUDA kernels; this
+module passes device pointers of torch tensors and the current CUDA stream.
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+
+Main entry points:
+
+* :class:`Foam` -- a packed scene (sites, Delaunay CSR adjacency, density and
+  SH attributes) resident on the GPU;
+* :meth:`Foam.render` / :meth:`Foam.backward` -- ``rf_render_fwd`` /
+  ``rf_render_bwd``;
+* :func:`render` -- differentiable render (``torch.autograd.Function``) with
+  respect to density, SH coefficients and site positions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+RF_OK = 0
+RF_F32, RF_BF16, RF_F16 = 0, 1, 2
+RAY_OK, RAY_MAX_STEPS = 0, 1
+_DTYPES = {torch.float32: RF_F32, torch.bfloat16: RF_BF16, torch.float16: RF_F16}
+
+
+class rf_camera(ctypes.Structure):
+    _fields_ = [("c2w", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("t_near", ctypes.c_float), ("t_far", ctypes.c_float)]
+
+
+class rf_scene_desc(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("pos", ctypes.c_void_p), ("adj_off", ctypes.c_void_p),
+                ("adj_idx", ctypes.c_void_p), ("density", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p), ("sh_degree", ctypes.c_int32),
+                ("attr_dtype", ctypes.c_int32), ("aabb_min", ctypes.c_float * 3),
+                ("aabb_max", ctypes.c_float * 3)]
+
+
+class rf_render_opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("max_steps", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+class RFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rf error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.c_void_p
+_S = ctypes.c_int32
+
+# name -> (restype, argtypes); every symbol include/rf.h declares
+SIGNATURES = {
+    "rf_version": (ctypes.c_int32, []),
+    "rf_last_error": (ctypes.c_char_p, []),
+    "rf_scene_create": (_S, [ctypes.POINTER(rf_scene_desc), _P, ctypes.POINTER(_P)]),
+    "rf_scene_set_attributes": (_S, [_P, _P, _P, ctypes.c_int32]),
+    "rf_scene_update_positions": (_S, [_P, _P, _P]),
+    "rf_scene_info": (_S, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_size_t)]),
+    "rf_scene_destroy": (_S, [_P]),
+    "rf_render_fwd": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.c_int32,
+                           ctypes.POINTER(rf_render_opts), _P, _P, _P, _P, _P, _P]),
+    "rf_render_bwd": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.c_int32,
+                           ctypes.POINTER(rf_render_opts), _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                           _P]),
+    "rf_trace_cells": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.POINTER(rf_render_opts),
+                            ctypes.c_int32, _P, _P, _P]),
+    "rf_mse_grad": (_S, [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load librf.so (building it with nvcc if absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"{path} not built")
+                _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != RF_OK:
+        raise RFError(rc, lib().rf_last_error().decode(errors="replace"))
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def camera_struct(cam) -> rf_camera:
+    c = rf_camera()
+    c.c2w[:] = [float(v) for v in np.asarray(cam.c2w, np.float32).reshape(-1)]
+    c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.t_near, c.t_far = cam.t_near, cam.t_far
+    return c
+
+
+def camera_array(cams) -> "ctypes.Array":
+    cams = list(cams) if isinstance(cams, (list, tuple)) else [cams]
+    arr = (rf_camera * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k] = camera_struct(c)
+    return arr
+
+
+def opts_struct(eps: float = 1e-4, max_steps: int = 0) -> rf_render_opts:
+    o = rf_render_opts()
+    o.eps = float(eps)
+    o.max_steps = int(max_steps)
+    return o
+
+
+def n_rays_of(cams) -> int:
+    cams = list(cams) if isinstance(cams, (list, tuple)) else [cams]
+    return sum(int(c.width) * int(c.height) for c in cams)
+
+
+class Foam:
+    """A Voronoi foam packed for traversal on the current CUDA device.
+
+    ``pos`` [N,3] float32, ``adj_off`` [N+1] / ``adj_idx`` [E] int32 and the
+    attributes ``density`` [N] and ``sh`` [N,(deg+1)^2,3] (float32, bfloat16
+    or float16) are CUDA tensors.  The attributes are borrowed by the library:
+    this object keeps references to them.
+    """
+
+    def __init__(self, pos, adj_off, adj_idx, density, sh, aabb=None, stream=None):
+        L = lib()
+        self.pos = pos.contiguous()
+        self.adj_off = adj_off.to(torch.int32).contiguous()
+        self.adj_idx = adj_idx.to(torch.int32).contiguous()
+        self._attrs(density, sh)
+        d = rf_scene_desc()
+        d.n_sites = int(self.pos.shape[0])
+        d.n_edges = int(self.adj_idx.shape[0])
+        d.pos = _ptr(self.pos).value
+        d.adj_off = _ptr(self.adj_off).value
+        d.adj_idx = _ptr(self.adj_idx).value if d.n_edges else None
+        d.density = _ptr(self.density).value
+        d.sh = _ptr(self.sh).value
+        d.sh_degree = self.sh_degree
+        d.attr_dtype = self.attr_dtype
+        if aabb is None:
+            d.aabb_min[:] = [1.0, 1.0, 1.0]
+            d.aabb_max[:] = [0.0, 0.0, 0.0]  # min > max: computed on the device
+        else:
+            d.aabb_min[:] = [float(v) for v in aabb[0]]
+            d.aabb_max[:] = [float(v) for v in aabb[1]]
+        h = ctypes.c_void_p()
+        _check(L.rf_scene_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self._pos_version = self.pos._version
+
+    def _attrs(self, density, sh):
+        if density.dtype not in _DTYPES or sh.dtype != density.dtype:
+            raise ValueError("density and sh must share one of float32/bfloat16/float16")
+        self.density = density.contiguous()
+        self.sh = sh.contiguous()
+        K = int(self.sh.shape[1])
+        deg = int(round(K ** 0.5)) - 1
+        if (deg + 1) ** 2 != K or self.sh.shape[2] != 3 or not 0 <= deg <= 3:
+            raise ValueError("sh must be [N,(deg+1)^2,3] with deg <= 3")
+        self.sh_degree = deg
+        self.attr_dtype = _DTYPES[density.dtype]
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda", attr_dtype=torch.float32, stream=None):
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+        return cls(t(scene.pos, torch.float32), t(scene.adj_off, torch.int32),
+                   t(scene.adj_idx, torch.int32), t(scene.density, attr_dtype),
+                   t(scene.sh, attr_dtype),
+                   aabb=(scene.aabb_min, scene.aabb_max), stream=stream)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("foam is closed")
+        return self._h
+
+    @property
+    def n_sites(self) -> int:
+        return int(self.pos.shape[0])
+
+    def info(self) -> dict:
+        n, e = ctypes.c_int64(), ctypes.c_int64()
+        box = (ctypes.c_float * 6)()
+        b = ctypes.c_size_t()
+        _check(lib().rf_scene_info(self.handle, ctypes.byref(n), ctypes.byref(e), box,
+                                   ctypes.byref(b)))
+        return dict(n_sites=n.value, n_edges=e.value, aabb=list(box), device_bytes=b.value)
+
+    def set_attributes(self, density, sh):
+        self._attrs(density, sh)
+        _check(lib().rf_scene_set_attributes(self.handle, _ptr(self.density), _ptr(self.sh),
+                                             self.attr_dtype))
+
+    def update_positions(self, pos=None, stream=None):
+        if pos is not None:
+            self.pos = pos.contiguous()
+        _check(lib().rf_scene_update_positions(self.handle, _ptr(self.pos), _stream(stream)))
+        self._pos_version = self.pos._version
+
+    def _sync_positions(self, pos):
+        if pos is not None and (pos is not self.pos or pos._version != self._pos_version):
+            self.update_positions(pos.detach())
+
+    def render(self, cams, eps: float = 1e-4, max_steps: int = 0, steps: bool = False,
+               status: bool = False, out=None, stream=None) -> dict:
+        """Forward render; returns rgb [R,3], trans [R], depth [R] (+ steps,
+        status) as CUDA tensors, rays of the cameras concatenated."""
+        ca = camera_array(cams)
+        R = n_rays_of(cams)
+        dev = self.pos.device
+        if out is None:
+            out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
+                       depth=torch.empty(R, device=dev))
+            if steps:
+                out["steps"] = torch.empty(R, dtype=torch.int32, device=dev)
+            if status:
+                out["status"] = torch.empty(R, dtype=torch.uint8, device=dev)
+        o = opts_struct(eps, max_steps)
+        _check(lib().rf_render_fwd(self.handle, ca, len(ca), ctypes.byref(o), _ptr(out["rgb"]),
+                                   _ptr(out["trans"]), _ptr(out["depth"]),
+                                   _ptr(out.get("steps")), _ptr(out.get("status")),
+                                   _stream(stream)))
+        return out
+
+    def backward(self, cams, fwd: dict, d_rgb, d_trans=None, d_depth=None, grads=None,
+                 eps: float = 1e-4, max_steps: int = 0, stream=None) -> dict:
+        """Accumulate gradients (density, sh, pos; float32) of the forward
+        outputs into ``grads`` (zero-initialised if None)."""
+        if grads is None:
+            dev = self.pos.device
+            grads = dict(density=torch.zeros(self.n_sites, device=dev),
+                         sh=torch.zeros(tuple(self.sh.shape), device=dev),
+                         pos=torch.zeros(self.n_sites, 3, device=dev))
+        ca = camera_array(cams)
+        o = opts_struct(eps, max_steps)
+        _check(lib().rf_render_bwd(self.handle, ca, len(ca), ctypes.byref(o), _ptr(fwd["rgb"]),
+                                   _ptr(fwd["trans"]), _ptr(fwd.get("depth")), _ptr(d_rgb),
+                                   _ptr(d_trans), _ptr(d_depth), _ptr(grads.get("density")),
+                                   _ptr(grads.get("sh")), _ptr(grads.get("pos")),
+                                   _stream(stream)))
+        return grads
+
+    def trace(self, cam, max_per_ray: int = 256, eps: float = 1e-4, max_steps: int = 0,
+              stream=None):
+        """Visited cells per ray [R, max_per_ray] (-1 padded) and counts [R]."""
+        R = int(cam.width) * int(cam.height)
+        dev = self.pos.device
+        cells = torch.empty(R, max_per_ray, dtype=torch.int32, device=dev)
+        counts = torch.empty(R, dtype=torch.int32, device=dev)
+        o = opts_struct(eps, max_steps)
+        ca = camera_array([cam])
+        _check(lib().rf_trace_cells(self.handle, ca, ctypes.byref(o), int(max_per_ray),
+                                    _ptr(cells), _ptr(counts), _stream(stream)))
+        return cells, counts
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().rf_scene_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mse_grad(rgb, target, scale: float, loss=None, stream=None):
+    """d_rgb = 2 scale (rgb - target) and loss += scale * sum (rgb - target)^2
+    (both on the device)."""
+    d = torch.empty_like(rgb)
+    if loss is None:
+        loss = torch.zeros(1, device=rgb.device)
+    _check(lib().rf_mse_grad(_ptr(rgb), _ptr(target), rgb.numel(), float(scale), _ptr(d),
+                             _ptr(loss), _stream(stream)))
+    return d, loss
+
+
+class _Render(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, foam, cams, eps, max_steps, density, sh, pos):
+        foam._sync_positions(pos)
+        out = foam.render(cams, eps=eps, max_steps=max_steps)
+        ctx.foam, ctx.cams, ctx.eps, ctx.max_steps = foam, cams, eps, max_steps
+        ctx.dtypes = (density.dtype, sh.dtype)
+        ctx.save_for_backward(out["rgb"], out["trans"], out["depth"])
+        return out["rgb"], out["trans"], out["depth"]
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_trans, g_depth):
+        rgb, trans, depth = ctx.saved_tensors
+        foam = ctx.foam
+        need = ctx.needs_input_grad
+        dev = rgb.device
+        grads = {}
+        if need[4]:
+            grads["density"] = torch.zeros(foam.n_sites, device=dev)
+        if need[5]:
+            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+        if need[6]:
+            grads["pos"] = torch.zeros(foam.n_sites, 3, device=dev)
+        if grads:
+            z = lambda g: None if g is None else g.contiguous().float()
+            foam.backward(ctx.cams, dict(rgb=rgb, trans=trans, depth=depth),
+                          z(g_rgb) if g_rgb is not None else torch.zeros_like(rgb),
+                          z(g_trans), z(g_depth), grads=grads, eps=ctx.eps,
+                          max_steps=ctx.max_steps)
+        gd = grads.get("density")
+        gs = grads.get("sh")
+        return (None, None, None, None,
+                None if gd is None else gd.to(ctx.dtypes[0]),
+                None if gs is None else gs.to(ctx.dtypes[1]),
+                grads.get("pos"))
+
+
+def render(foam: Foam, cams, density=None, sh=None, pos=None, eps: float = 1e-4,
+           max_steps: int = 0):
+    """Differentiable render of ``cams``: returns (rgb [R,3], trans [R],
+    depth [R]); gradients flow to ``density``, ``sh`` and ``pos`` (defaults:
+    the foam's own tensors).  A changed ``pos`` is re-packed first."""
+    density = foam.density if density is None else density
+    sh = foam.sh if sh is None else sh
+    if density is not foam.density or sh is not foam.sh:
+        foam.set_attributes(density.detach(), sh.detach())
+    if pos is None:
+        pos = foam.pos
+    return _Render.apply(foam, cams, eps, max_steps, density, sh, pos)
