@@ -3,9 +3,9 @@
  *
  * Differentiable ray tracing through a 3D Voronoi foam (Govindarajan et al.,
  * "Radiant Foam: Real-Time Differentiable Ray Tracing", arXiv 2502.01157).
- * The scene is a set of sites p_i (Sec. 3.2, Eq. 4); each Voronoi cell carries
+ * The scene is a set of sites p_i (Sec. 3.2, Eq. 5); each Voronoi cell carries
  * a density sigma_i and spherical-harmonic colour coefficients (Sec. 3.4).
- * Rays walk cell to cell (Alg. 1) and composite Eq. (2)-(3).
+ * Rays walk cell to cell (Alg. 1) and composite Eq. (3)-(4).
  *
  * Conventions for every call:
  *   - Pointers documented "device" are CUDA device pointers owned by the
@@ -163,7 +163,7 @@ RF_API rf_status rf_scene_info(const rf_scene *scene, int64_t *n_sites, int64_t 
 RF_API rf_status rf_scene_destroy(rf_scene *scene);
 
 /*
- * Forward render of n_cams cameras in one launch (Alg. 1 per ray, Eq. 2-3).
+ * Forward render of n_cams cameras in one launch (Alg. 1 per ray, Eq. 3-4).
  * Outputs are concatenated camera after camera (ray r of camera c at
  * sum_{c'<c} W_c' H_c' + r):
  *   rgb    device float [R][3]   composited colour (black background).

@@ -11,7 +11,7 @@ function follows the paper's statement of the method:
 * :func:`camera_rays`  -- pinhole rays through pixel centres (the inputs o, d
   of Alg. 1).
 * :func:`nearest_site` -- nn(o), the initial cell of Alg. 1.
-* :func:`render`       -- Alg. 1 with Eq. (2)-(3) compositing (Sec. 3.1-3.2).
+* :func:`render`       -- Alg. 1 with Eq. (3)-(4) compositing (Sec. 3.1-3.2).
 * :func:`render_bwd`   -- reverse-mode gradient of the rendered outputs; sites
   receive gradient only through segment widths (Sec. 3.1).
 * :func:`sh_basis`     -- real spherical harmonics of degree <= 3 (Sec. 3.4).
@@ -153,7 +153,7 @@ def nearest_site(pos, q):
 
 def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
            tau=None, trace: int = 0, threads: int = 0) -> dict:
-    """Forward render (Alg. 1, Eq. 2).  Returns rgb [R,3], trans [R], depth [R],
+    """Forward render (Alg. 1, Eq. 3-4).  Returns rgb [R,3], trans [R], depth [R],
     steps [R], status [R], degen [R] and, if ``trace > 0``, trace_cells
     [R,trace] (-1 padded) and trace_t [R,trace]."""
     S = _SceneF64(scene)

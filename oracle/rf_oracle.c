@@ -16,7 +16,7 @@
  *     whose normal x_j - x_i makes an angle below 90 deg with d is an exit
  *     (Fig. 3); the nearest exit (strict <, first in adjacency order on ties)
  *     gives t_1 and the next cell.
- *   - Piecewise-constant compositing, Eq. (2)-(3): alpha = 1 - exp(-sigma
+ *   - Piecewise-constant compositing, Eq. (3)-(4): alpha = 1 - exp(-sigma
  *     delta), C += T alpha c, T *= (1 - alpha), while T > eps.
  *   - Colour from real spherical harmonics of degree <= 3 in the ray
  *     direction, plus 0.5, clamped at 0 (Sec. 3.4 "Training").

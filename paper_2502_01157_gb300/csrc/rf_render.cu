@@ -21,7 +21,7 @@ struct FwdOut {
     int32_t max_trace;
 };
 
-// Forward: Alg. 1 per ray with Eq. (2)-(3) compositing.
+// Forward: Alg. 1 per ray with Eq. (3)-(4) compositing.
 template <typename AT, int DEG, bool TRACE>
 __global__ void __launch_bounds__(kBlock) fwd_kernel(const RenderParams p, const FwdOut out) {
     const PixelTask px = pixel_of_thread(p.lc);

@@ -2,8 +2,8 @@
 
 Each test checks the oracle against something other than itself:
 
-* the Voronoi definition, Eq. (4), by brute force over all sites;
-* closed forms of Eq. (2)-(3) (homogeneous media, empty media, a two-cell
+* the Voronoi definition, Eq. (5), by brute force over all sites;
+* closed forms of Eq. (3)-(4) (homogeneous media, empty media, a two-cell
   scene and an early-stop chain derived by hand);
 * the real spherical harmonics against scipy and against orthonormality;
 * the analytic backward against central finite differences of the forward;
@@ -106,7 +106,7 @@ def test_nearest_site_is_bruteforce_argmin():
 
 
 # ---------------------------------------------------------------------------
-# The walk against the Voronoi definition (Eq. 4) by brute force
+# The walk against the Voronoi definition (Eq. 5) by brute force
 # ---------------------------------------------------------------------------
 def _nearest(pos, p):
     dd = np.sum((pos[None, :, :] - p[:, None, :]) ** 2, axis=2)
@@ -182,7 +182,7 @@ def test_segment_widths_sum_to_the_clipped_ray_length():
 
 
 # ---------------------------------------------------------------------------
-# Closed forms of Eq. (2)-(3)
+# Closed forms of Eq. (3)-(4)
 # ---------------------------------------------------------------------------
 Y00 = 1 / (2 * math.sqrt(math.pi))
 
