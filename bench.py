@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
+    ap.add_argument("--sites", type=int, default=0, help="override the workload's site count")
     ap.add_argument("--no-extras", action="store_true", help="skip dtype variants / serving")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -174,7 +175,7 @@ def run_reference(args):
     import oracle
     from paper_2502_01157_gb300 import scenes as S
 
-    scene = S.config_scene(args.workload)
+    scene = S.config_scene(args.workload, n_sites=args.sites or None)
     cam = rank_camera(args.workload, 0)
     target = S.random_target(cam.n_rays, 2024)
     rng = np.random.default_rng(5)
@@ -217,7 +218,7 @@ def main():
     from paper_2502_01157_gb300 import scenes as S
 
     # scene generation uses a spawn process pool: do it before CUDA starts
-    scene = S.config_scene(args.workload)
+    scene = S.config_scene(args.workload, n_sites=args.sites or None)
     cam = rank_camera(args.workload, rank)
     target_np = S.random_target(cam.n_rays, 2024 + rank)
 
@@ -369,7 +370,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}"
+                                   + (f" (with {scene.n_sites} sites)" if args.sites else ""),
                        "n_sites": scene.n_sites, "n_edges": scene.n_edges, "rays_per_step": R,
                        "cell_steps_per_ray": steps_total / R, "sh_degree": deg,
                        "step": "fwd + mse grad + bwd (FP32 attributes)",
