@@ -209,6 +209,41 @@ RF_API rf_status rf_trace_cells(rf_scene *scene, const rf_camera *cam,
                                 int32_t *cells, int32_t *counts, void *stream);
 
 /*
+ * Forward render that allocates no device memory (no counterpart in the
+ * paper; an interface of this library).  It is for callers that cannot call
+ * cudaMalloc -- code running under another runtime or engine that owns the
+ * device allocator and forbids allocations from outside, or a latency-bound
+ * render loop where an allocation would stall -- and so cannot create an
+ * rf_scene, whose packed copy and workspace are allocated.
+ *
+ * Inputs are the caller's own device arrays, as in rf_scene_desc (pos
+ * [n_sites][3], adj_off [n_sites+1], adj_idx [n_edges], density, sh), plus
+ * the scene box aabb6 (HOST, min xyz then max xyz, min <= max required);
+ * outputs rgb [R][3], trans [R], depth [R] as in rf_render_fwd, with the same
+ * values (the face records are formed on the fly with the packer's FP32
+ * operations).  The adjacency is not validated; out-of-range offsets or ids
+ * end the affected ray instead of being read.
+ *
+ * Its only scratch, one 64-bit start-cell key per camera, lives in a fixed
+ * device array inside the library (64 entries, 512 bytes, held on every
+ * device that loads the library until the process exits).  Hence:
+ *   - at most 64 cameras per call; more returns RF_ERR_INVALID_ARG;
+ *   - every call shares that array: calls that overlap on the GPU (on
+ *     different streams, or from different threads) race and must not be
+ *     issued concurrently; calls ordered on one stream are safe;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress), so make that first call before any stream
+ *     capture.
+ */
+RF_API rf_status rf_render_fwd_noalloc(int64_t n_sites, int64_t n_edges, const float *pos,
+                                       const int32_t *adj_off, const int32_t *adj_idx,
+                                       const void *density, const void *sh, int32_t sh_degree,
+                                       int32_t attr_dtype, const float *aabb6,
+                                       const rf_camera *cams, int32_t n_cams,
+                                       const rf_render_opts *opts, float *rgb, float *trans,
+                                       float *depth, void *stream);
+
+/*
  * MSE loss helper for a training step (device, n = 3 * rays):
  *   d_rgb[k] = 2 * scale * (rgb[k] - target[k]);  *loss += scale * sum_k (rgb[k]-target[k])^2
  * loss is a device float accumulated with atomics (zero it first).

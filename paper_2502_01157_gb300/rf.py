@@ -81,6 +81,10 @@ SIGNATURES = {
     "rf_trace_cells": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.POINTER(rf_render_opts),
                             ctypes.c_int32, _P, _P, _P]),
     "rf_mse_grad": (_S, [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
+    "rf_render_fwd_noalloc": (_S, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
+                                   ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(rf_camera), ctypes.c_int32,
+                                   ctypes.POINTER(rf_render_opts), _P, _P, _P, _P]),
 }
 
 
@@ -318,6 +322,29 @@ def mse_grad(rgb, target, scale: float, loss=None, stream=None):
     _check(lib().rf_mse_grad(_ptr(rgb), _ptr(target), rgb.numel(), float(scale), _ptr(d),
                              _ptr(loss), _stream(stream)))
     return d, loss
+
+
+def render_noalloc(pos, adj_off, adj_idx, density, sh, aabb, cams, eps: float = 1e-4,
+                   max_steps: int = 0, out=None, stream=None) -> dict:
+    """``rf_render_fwd_noalloc``: forward render straight from the caller's
+    arrays, with no device allocation inside the library (its only scratch is
+    a fixed 64-camera array).  Same outputs as :meth:`Foam.render`."""
+    ca = camera_array(cams)
+    R = n_rays_of(cams)
+    if out is None:
+        dev = pos.device
+        out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
+                   depth=torch.empty(R, device=dev))
+    K = int(sh.shape[1])
+    box = (ctypes.c_float * 6)(*[float(v) for v in list(aabb[0]) + list(aabb[1])])
+    o = opts_struct(eps, max_steps)
+    _check(lib().rf_render_fwd_noalloc(int(pos.shape[0]), int(adj_idx.shape[0]), _ptr(pos),
+                                       _ptr(adj_off), _ptr(adj_idx) if adj_idx.numel() else None,
+                                       _ptr(density), _ptr(sh), int(round(K ** 0.5)) - 1,
+                                       _DTYPES[density.dtype], box, ca, len(ca), ctypes.byref(o),
+                                       _ptr(out["rgb"]), _ptr(out["trans"]), _ptr(out["depth"]),
+                                       _stream(stream)))
+    return out
 
 
 class _Render(torch.autograd.Function):
