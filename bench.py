@@ -83,6 +83,33 @@ def bwd_extra_bytes_per_step(deg):
     return 2 * (4 + 12 * (deg + 1) ** 2 + 24)
 
 
+def kernel_source_hash():
+    """Hash of the CUDA sources the renderer's kernels are built from."""
+    import hashlib
+
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2502_01157_gb300", "csrc")
+    for name in ("rf_internal.cuh", "rf_render.cu", "rf_scene.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch of ``kernel`` on ``workload`` from the ncu
+    capture recorded in profiles/dram_traffic.txt, or None if that capture
+    was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == workload and f[2] == src:
+            return float(f[3])
+    return None
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -206,6 +233,94 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU
 # ---------------------------------------------------------------------------
+SERVE_RATES = (50, 200, 1000, 2000)
+
+
+def mixture_extras(scene, args, dev):
+    """The 3M-site mixture scene: 8 mixed-resolution cameras forward+backward
+    in one launch (FP32), batched forward FP32 vs BF16 on the serving poses,
+    and open-loop Poisson serving with BF16 attributes."""
+    import numpy as np
+    import torch
+    from paper_2502_01157_gb300 import rf
+    from paper_2502_01157_gb300 import scenes as S
+    from paper_2502_01157_gb300.serve import Server, run_open_loop
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    foam = rf.Foam.from_scene(scene)
+    cams = S.config_cameras("c4")
+    R = rf.n_rays_of(cams)
+    target = torch.rand(R, 3, device=dev)
+    grads = dict(density=torch.zeros(scene.n_sites, device=dev),
+                 sh=torch.zeros(scene.n_sites, 16, 3, device=dev),
+                 pos=torch.zeros(scene.n_sites, 3, device=dev))
+    out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
+               depth=torch.empty(R, device=dev))
+
+    def step():
+        foam.render(cams, out=out)
+        d, _ = rf.mse_grad(out["rgb"], target, 1.0 / (3 * R))
+        foam.backward(cams, out, d, grads=grads)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    n = max(3, args.steps // 2)
+    a, b, c = ev(), ev(), ev()
+    a.record()
+    for _ in range(n):
+        foam.render(cams, out=out)
+    b.record()
+    for _ in range(n):
+        step()
+    c.record()
+    torch.cuda.synchronize()
+    res = {"scene": f"c4/c5 mixture, {scene.n_sites} sites, SH deg 3",
+           "c4_cameras": "8 mixed (2x 640x480, 1280x720, 1600x900, 1920x1080) on a radius-12 sphere",
+           "c4_rays": R,
+           "c4_fwd_fp32_mrays_s": R * n / (a.elapsed_time(b) * 1e-3) / 1e6,
+           "c4_fwdbwd_fp32_mrays_s": R * n / (b.elapsed_time(c) * 1e-3) / 1e6}
+    # serving poses and resolutions
+    rng = np.random.default_rng(1005)
+    n_req = 4000
+    poses = S.sphere_poses(n_req, 12.0, 1005)
+    sizes = [S.C5_RESOLUTIONS[k] for k in rng.integers(0, 4, n_req)]
+    scams = [S.pinhole(w, h, 60.0, c2w=p) for (w, h), p in zip(sizes, poses)]
+    # batched forward of the first 64 serving requests, FP32 vs BF16 attributes
+    batch = scams[:16]
+    Rb = rf.n_rays_of(batch)
+    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        foam.set_attributes(torch.from_numpy(scene.density).to(dev, dt),
+                            torch.from_numpy(scene.sh).to(dev, dt))
+        foam.render(batch)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(n):
+            foam.render(batch)
+        b.record()
+        torch.cuda.synchronize()
+        res[f"serve_poses_batched_fwd_{name}_mrays_s"] = Rb * n / (a.elapsed_time(b) * 1e-3) / 1e6
+    # open-loop Poisson serving with BF16 attributes (set just above)
+    srv = Server(foam, mem_budget_bytes=4 << 30, max_inflight=512, n_streams=4, max_batch=8)
+    rates = []
+    for k, rate in enumerate(SERVE_RATES):
+        m = int(min(n_req, max(100, rate * 2)))
+        arr = S.poisson_arrivals(float(rate), m, 500 + k)
+        st = run_open_loop(srv, scams[:m], arr, deadline_s=60.0)
+        rates.append({"rate_req_s": rate, "offered": m, "completed": st["completed"],
+                      "rejected": st["rejected_open_loop"], "p50_ms": st["p50_ms"],
+                      "p99_ms": st["p99_ms"], "mrays_s": st["mrays_s"],
+                      "mean_batch": st["mean_batch"], "max_busy_streams": st["max_busy_streams"]})
+    srv.close()
+    res["serving_bf16"] = {"budget_gb": 4, "streams": 4, "max_batch": 8,
+                           "resolutions": "uniform over 320x240, 640x480, 1280x720, 1920x1080",
+                           "poses": "uniform on the radius-12 sphere, looking at the origin",
+                           "rates": rates}
+    foam.close()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -221,6 +336,9 @@ def main():
     scene = S.config_scene(args.workload, n_sites=args.sites or None)
     cam = rank_camera(args.workload, rank)
     target_np = S.random_target(cam.n_rays, 2024 + rank)
+    mix_scene = None
+    if not args.no_extras and world == 1:
+        mix_scene = S.config_scene("c4")  # 3M-site mixture: batched and serving workloads
 
     import torch
 
@@ -329,6 +447,10 @@ def main():
         foam.set_attributes(torch.from_numpy(scene.density).to(dev),
                             torch.from_numpy(scene.sh).to(dev))
 
+    mixture = None
+    if mix_scene is not None:
+        mixture = mixture_extras(mix_scene, args, dev)
+
     # end to end through the public API with host buffers
     pin_t = torch.from_numpy(target_np).pin_memory()
     pin_rgb = torch.empty(R, 3).pin_memory()
@@ -363,7 +485,10 @@ def main():
     achieved = kb / (kms * 1e-3) / 1e9
     roof = {"kernel": f"rf::{dominant}_kernel<float,{deg}>", "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "bytes_per_cell_step": (bytes_per_step(k_bar, deg, attr_b) +
+            "traffic": measured_traffic(f"{dominant}_kernel<float,{deg}>", args.workload if not args.sites else f"{args.workload}@{scene.n_sites}"),
+            "algorithmic_bytes_per_launch": kb, "kernel_source": kernel_source_hash(),
+            "note": "algorithmic bytes are served >99% by L1/L2 (traffic = ncu DRAM bytes per "
+                    "launch); the binding unit is the L1 load data path, see profiles/", "bytes_per_cell_step": (bytes_per_step(k_bar, deg, attr_b) +
                                                      (bwd_extra_bytes_per_step(deg) if dominant == "bwd" else 0)),
             "cell_steps_per_launch": steps_total, "ms_per_launch": kms}
 
@@ -380,6 +505,7 @@ def main():
             "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
             "cell_steps_per_s": steps_total / (ms * 1e-3),
             **res,
+            "mixture_3m": mixture,
             "gpu_launches": args.steps * 5,
             "roofline": roof,
             "clocks": clk,

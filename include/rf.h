@@ -209,6 +209,64 @@ RF_API rf_status rf_trace_cells(rf_scene *scene, const rf_camera *cam,
                                 int32_t *cells, int32_t *counts, void *stream);
 
 /*
+ * Serving: continuous batching of render requests over a resident scene
+ * (the paper's renderer, Sec. 3.4, turned into a request loop).
+ *
+ *   mem_budget_bytes  device memory reserved for in-flight outputs: 20 B per
+ *                     ray (rgb, T, depth); the same number of rays x 12 B of
+ *                     pinned host memory receives the images.  A request is
+ *                     admitted only if its rays fit in the free part.
+ *   max_inflight      admitted requests not yet collected.
+ *   n_streams         batches that may run on the device at the same time.
+ *   max_batch         cameras (any resolutions) per launch, 1..16.
+ *   eps, max_steps    as in rf_render_opts.
+ *
+ * A scheduler thread launches waiting admitted requests, up to max_batch at a
+ * time, on any free stream; requests that arrive while others run start as
+ * soon as a stream frees up.  Images are bit-identical to rf_render_fwd of
+ * the same camera (rays are independent).  The server borrows the scene,
+ * which must outlive it.  All calls are thread-safe.
+ */
+typedef struct rf_serve_config {
+    size_t mem_budget_bytes;
+    int32_t max_inflight;
+    int32_t n_streams;
+    int32_t max_batch;
+    float eps;
+    int32_t max_steps;
+} rf_serve_config;
+
+typedef struct rf_serve_metrics {
+    int64_t completed;     /* requests rendered (since creation or the last reset) */
+    int64_t rejected;      /* submits refused (RF_ERR_BUSY or too large) */
+    int64_t rays_done;
+    int64_t batches;       /* launches */
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* latency: submit -> image in host memory */
+    double mrays_s;        /* rays_done / (last completion - first submit) */
+    double mean_batch;     /* requests per launch */
+    int32_t max_busy_streams;
+    int32_t inflight;
+} rf_serve_metrics;
+
+typedef struct rf_server rf_server;
+
+RF_API rf_status rf_serve_create(rf_scene *scene, const rf_serve_config *cfg, rf_server **out);
+/* Admits one request (cam: host) or returns RF_ERR_BUSY (no memory / slot);
+ * RF_ERR_INVALID_ARG if it can never fit. */
+RF_API rf_status rf_serve_submit(rf_server *srv, const rf_camera *cam, uint64_t *req_id);
+/* *done = 1 once rendered; then the image (rgb, [H*W][3] floats) is copied to
+ * host_rgb (may be NULL), the latency reported and the request released. */
+RF_API rf_status rf_serve_poll(rf_server *srv, uint64_t req_id, float *host_rgb, int32_t *done,
+                               double *latency_ms);
+/* As rf_serve_poll but waits up to timeout_ms (RF_ERR_TIMEOUT after). */
+RF_API rf_status rf_serve_wait(rf_server *srv, uint64_t req_id, int32_t timeout_ms, float *host_rgb,
+                               double *latency_ms);
+RF_API rf_status rf_serve_stats(rf_server *srv, rf_serve_metrics *out);
+RF_API rf_status rf_serve_reset_stats(rf_server *srv);
+/* Stops the scheduler, waits for launched work, frees the pools. */
+RF_API rf_status rf_serve_destroy(rf_server *srv);
+
+/*
  * Forward render that allocates no device memory (no counterpart in the
  * paper; an interface of this library).  It is for callers that cannot call
  * cudaMalloc -- code running under another runtime or engine that owns the

@@ -13,16 +13,18 @@
 struct rf_scene {
     int64_t n_sites = 0;
     int64_t n_edges = 0;
-    float4 *cells = nullptr;     // [N]
-    int32_t *off = nullptr;      // [N+1]
-    float4 *faces = nullptr;     // [E]
+    float4 *cells = nullptr;     // [N]: {x, y, z, begin}
+    int32_t *off = nullptr;      // [N+1] offsets of the padded face lists (ends = off + 1)
+    float4 *faces = nullptr;     // [n_slots] face records (even-aligned, even-length lists)
+    int64_t n_slots = 0;
     const void *density = nullptr;  // borrowed
     const void *sh = nullptr;       // borrowed
     int32_t sh_degree = 0;
     int32_t attr_dtype = RF_F32;
     float box[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long *start_keys = nullptr;  // workspace [kMaxCamsPerLaunch]
-    int32_t *flags = nullptr;                  // workspace [4] (validation counters)
+    int32_t *flags = nullptr;                  // workspace [8] (validation counters)
+    int32_t sh_v8 = 0;                         // SH rows 32-byte aligned
     size_t bytes = 0;
     int device = 0;
 };

@@ -26,22 +26,26 @@ constexpr int kDefaultMaxSteps = 1 << 16;
 
 // ---------------------------------------------------------------------------
 // Packed scene (device memory owned by rf_scene)
-//   cells[i] = {x_i, y_i, z_i, bits(first face index)}
-//   off[i]   = first face of cell i (off[N] = E); count = off[i+1] - off[i]
-//   faces[f] = {u_x, u_y, u_z, bits(j)} for the f-th directed edge (i, j),
-//              u = 2 (p_j - p_i) / |p_j - p_i|^2.
+//   cells[i] = {x_i, y_i, z_i, bits(begin)}, ends[i] = end of the face list
+//       (the forward is bound by the bytes the L1 delivers to the lanes, so
+//       the header is kept at 20 bytes)
+//   faces[f] = {u_x, u_y, u_z, bits(j)} for the directed edge (i, j),
+//       u = 2 (p_j - p_i) / |p_j - p_i|^2.  Each cell's list starts at an
+//       even index and has an even length (padded with {0, 0, 0, -1}, which
+//       is never front-facing), so faces are read two per 256-bit load.
 // With o~ = o - p_i the bisector of (p_i, p_j) is crossed at
 //   t = (1 - u . o~) / (u . d),
 // front-facing (an exit, Fig. 3) iff u . d > 0.
 // ---------------------------------------------------------------------------
 struct SceneDev {
     const float4 *cells;
-    const int32_t *off;
+    const int32_t *ends;
     const float4 *faces;
     const void *density;
     const void *sh;
     float box_lo[3];
     float box_hi[3];
+    int32_t sh_v8;  // SH rows are 32-byte aligned (base and row size)
 };
 
 // Cameras of one launch and the tile partition of their images.
@@ -67,6 +71,24 @@ struct RenderParams {
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// 256-bit read-only load (sm_100+); p must be 32-byte aligned.
+__device__ __forceinline__ void ldg256(const void *p, uint32_t (&v)[8]) {
+    asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7])
+        : "l"(p));
+}
+
+struct CellHdr {
+    float x, y, z;
+    int begin, end;
+};
+
+__device__ __forceinline__ CellHdr load_cell(const SceneDev &s, int i) {
+    const float4 h = __ldg(s.cells + i);
+    return {h.x, h.y, h.z, __float_as_int(h.w), __ldg(s.ends + i)};
+}
 
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -194,31 +216,56 @@ __device__ __forceinline__ void unpack16<__half>(const uint4 &q, float *out) {
 }
 
 // Colour before the clamp: pre[ch] = sum_k sh[i][k][ch] Y_k + 0.5, summed in
-// increasing k (Sec. 3.4).
+// increasing k (Sec. 3.4).  Rows whose size is a multiple of 32 bytes are read
+// with 256-bit loads when the base is 32-byte aligned (v8), else with 128-bit
+// loads when possible, else element by element; the sum order is the same.
 template <typename AT, int DEG>
 __device__ __forceinline__ void sh_colour(const AT *__restrict__ sh, int i, const float *Y,
-                                          float *pre) {
+                                          float *pre, bool v8) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int NV = 3 * K;
+    constexpr int RB = NV * (int)sizeof(AT);
     float acc[3] = {0.f, 0.f, 0.f};
-    if constexpr ((NV * sizeof(AT)) % 16 == 0) {
-        constexpr int EPV = 16 / sizeof(AT);
-        constexpr int NQ = NV / EPV;
-        const uint4 *row = reinterpret_cast<const uint4 *>(sh + (size_t)i * NV);
+    bool done = false;
+    if constexpr (RB % 32 == 0) {
+        if (v8) {
+            constexpr int EPV = 16 / sizeof(AT);
+            const char *row = reinterpret_cast<const char *>(sh) + (size_t)i * RB;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            float v[EPV];
-            unpack16<AT>(ldg(row + q), v);
+            for (int q = 0; q < RB / 32; ++q) {
+                uint32_t w[8];
+                ldg256(row + 32 * q, w);
+                float v[2 * EPV];
+                unpack16<AT>(make_uint4(w[0], w[1], w[2], w[3]), v);
+                unpack16<AT>(make_uint4(w[4], w[5], w[6], w[7]), v + EPV);
 #pragma unroll
-            for (int e = 0; e < EPV; ++e) {
-                const int g = q * EPV + e;
-                acc[g % 3] = __fmaf_rn(v[e], Y[g / 3], acc[g % 3]);
+                for (int e = 0; e < 2 * EPV; ++e) {
+                    const int g = q * 2 * EPV + e;
+                    acc[g % 3] = __fmaf_rn(v[e], Y[g / 3], acc[g % 3]);
+                }
             }
+            done = true;
         }
-    } else {
-        const AT *row = sh + (size_t)i * NV;
+    }
+    if (!done) {
+        if constexpr (RB % 16 == 0) {
+            constexpr int EPV = 16 / sizeof(AT);
+            const uint4 *row = reinterpret_cast<const uint4 *>(sh + (size_t)i * NV);
 #pragma unroll
-        for (int g = 0; g < NV; ++g) acc[g % 3] = __fmaf_rn(to_f(ldg(row + g)), Y[g / 3], acc[g % 3]);
+            for (int q = 0; q < RB / 16; ++q) {
+                float v[EPV];
+                unpack16<AT>(ldg(row + q), v);
+#pragma unroll
+                for (int e = 0; e < EPV; ++e) {
+                    const int g = q * EPV + e;
+                    acc[g % 3] = __fmaf_rn(v[e], Y[g / 3], acc[g % 3]);
+                }
+            }
+        } else {
+            const AT *row = sh + (size_t)i * NV;
+#pragma unroll
+            for (int g = 0; g < NV; ++g) acc[g % 3] = __fmaf_rn(to_f(ldg(row + g)), Y[g / 3], acc[g % 3]);
+        }
     }
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) pre[ch] = __fadd_rn(acc[ch], 0.5f);
@@ -227,22 +274,33 @@ __device__ __forceinline__ void sh_colour(const AT *__restrict__ sh, int i, cons
 // Exit face of cell i (Alg. 1 inner loop): the front-facing bisector with the
 // smallest crossing parameter, first in adjacency order on ties.  The
 // comparison t_j < t_best is done by cross-multiplication (both denominators
-// are positive), so no division is needed per face.  Returns j or -1.
+// are positive), so no division is needed per face.  Faces come in pairs
+// (one 256-bit load); padding records have u = 0 and are never exits.
+// Returns j or -1.
+__device__ __forceinline__ void face_test(uint32_t ux, uint32_t uy, uint32_t uz, uint32_t j,
+                                          const float3 &d, const float3 &oc, float &nb, float &db,
+                                          int &jb) {
+    const float x = __uint_as_float(ux), y = __uint_as_float(uy), z = __uint_as_float(uz);
+    const float den = __fmaf_rn(x, d.x, __fmaf_rn(y, d.y, __fmul_rn(z, d.z)));
+    const float num = __fmaf_rn(-x, oc.x, __fmaf_rn(-y, oc.y, __fmaf_rn(-z, oc.z, 1.f)));
+    if (den > 0.f && __fmul_rn(num, db) < __fmul_rn(nb, den)) {
+        nb = num;
+        db = den;
+        jb = (int)j;
+    }
+}
+
 __device__ __forceinline__ int find_exit(const float4 *__restrict__ faces, int begin, int end,
                                          const float3 &d, const float3 &oc, float &num_best,
                                          float &den_best) {
     float nb = 1.f, db = 0.f;
     int jb = -1;
-#pragma unroll 4
-    for (int f = begin; f < end; ++f) {
-        const float4 r = ldg(faces + f);
-        const float den = __fmaf_rn(r.x, d.x, __fmaf_rn(r.y, d.y, __fmul_rn(r.z, d.z)));
-        const float num = __fmaf_rn(-r.x, oc.x, __fmaf_rn(-r.y, oc.y, __fmaf_rn(-r.z, oc.z, 1.f)));
-        if (den > 0.f && __fmul_rn(num, db) < __fmul_rn(nb, den)) {
-            nb = num;
-            db = den;
-            jb = __float_as_int(r.w);
-        }
+#pragma unroll 2
+    for (int f = begin; f < end; f += 2) {
+        uint32_t v[8];
+        ldg256(faces + f, v);
+        face_test(v[0], v[1], v[2], v[3], d, oc, nb, db, jb);
+        face_test(v[4], v[5], v[6], v[7], d, oc, nb, db, jb);
     }
     num_best = nb;
     den_best = db;
@@ -261,14 +319,12 @@ struct Segment {
 };
 
 template <typename AT, int DEG>
-__device__ __forceinline__ void cell_step(const SceneDev &s, int i, const float4 &cell,
+__device__ __forceinline__ void cell_step(const SceneDev &s, int i, const CellHdr &cell,
                                           const float3 &o, const float3 &d, float t0, float tmin,
                                           float tmax, const float *Y, Segment &g, float3 &oc) {
-    const int begin = __float_as_int(cell.w);
-    const int end = ldg(s.off + i + 1);
     oc = make_float3(__fsub_rn(o.x, cell.x), __fsub_rn(o.y, cell.y), __fsub_rn(o.z, cell.z));
     float nb, db;
-    g.next = find_exit(s.faces, begin, end, d, oc, nb, db);
+    g.next = find_exit(s.faces, cell.begin, cell.end, d, oc, nb, db);
     g.t1 = g.next >= 0 ? __fdiv_rn(nb, db) : __int_as_float(0x7f800000);
     g.a = t0 > tmin ? t0 : tmin;
     g.b = g.t1 < tmax ? g.t1 : tmax;
@@ -276,7 +332,7 @@ __device__ __forceinline__ void cell_step(const SceneDev &s, int i, const float4
     g.delta = w > 0.f ? w : 0.f;
     g.sigma = to_f(ldg(reinterpret_cast<const AT *>(s.density) + i));
     g.e = expf(-__fmul_rn(g.sigma, g.delta));
-    sh_colour<AT, DEG>(reinterpret_cast<const AT *>(s.sh), i, Y, g.pre);
+    sh_colour<AT, DEG>(reinterpret_cast<const AT *>(s.sh), i, Y, g.pre, s.sh_v8 != 0);
 }
 
 }  // namespace rf

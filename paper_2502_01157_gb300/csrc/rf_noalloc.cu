@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) raw_fwd_kernel(const RawParams p, floa
             const float sigma = to_f(__ldg(reinterpret_cast<const AT *>(p.s.density) + i));
             const float e = expf(-__fmul_rn(sigma, delta));
             float pre[3];
-            sh_colour<AT, DEG>(reinterpret_cast<const AT *>(p.s.sh), i, Y, pre);
+            sh_colour<AT, DEG>(reinterpret_cast<const AT *>(p.s.sh), i, Y, pre, false);
             const float w = __fmul_rn(T, __fsub_rn(1.f, e));
             C0 = __fmaf_rn(w, fmaxf(pre[0], 0.f), C0);
             C1 = __fmaf_rn(w, fmaxf(pre[1], 0.f), C1);

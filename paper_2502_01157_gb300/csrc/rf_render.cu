@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const RenderParams p, const
                 st = RF_RAY_MAX_STEPS;
                 break;
             }
-            const float4 cell = ldg(p.s.cells + i);
+            const CellHdr cell = load_cell(p.s, i);
             Segment g;
             float3 oc;
             cell_step<AT, DEG>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc);
@@ -84,25 +84,6 @@ struct BwdIO {
     int32_t sh_vec;  // g_sh rows may use 16-byte atomics
 };
 
-// Position gradient of one crossing of the bisector of (p_a, p_b) at t:
-// dt/dp_b = (p_b - x)/den, dt/dp_a = (x - p_a)/den with x = o + t d,
-// den = (p_b - p_a).d; oca = o - p_a.
-__device__ __forceinline__ void scatter_crossing(float *__restrict__ g_pos, int ia, const float3 &xa,
-                                                 const float3 &oca, int ib, const float3 &xb,
-                                                 float t, const float3 &d, float adj) {
-    if (!g_pos || adj == 0.f) return;
-    const float nx = xb.x - xa.x, ny = xb.y - xa.y, nz = xb.z - xa.z;
-    const float den = nx * d.x + ny * d.y + nz * d.z;
-    const float px = oca.x + t * d.x, py = oca.y + t * d.y, pz = oca.z + t * d.z;  // x - p_a
-    const float s = adj / den;
-    atomicAdd(g_pos + 3 * (int64_t)ia + 0, s * px);
-    atomicAdd(g_pos + 3 * (int64_t)ia + 1, s * py);
-    atomicAdd(g_pos + 3 * (int64_t)ia + 2, s * pz);
-    atomicAdd(g_pos + 3 * (int64_t)ib + 0, s * (nx - px));
-    atomicAdd(g_pos + 3 * (int64_t)ib + 1, s * (ny - py));
-    atomicAdd(g_pos + 3 * (int64_t)ib + 2, s * (nz - pz));
-}
-
 template <int DEG>
 __device__ __forceinline__ void scatter_sh(float *__restrict__ g_sh, int i, const float *cb,
                                            const float *Y, bool vec) {
@@ -130,115 +111,248 @@ __device__ __forceinline__ void scatter_sh(float *__restrict__ g_sh, int i, cons
 
 // Backward: the walk of the forward is repeated with identical arithmetic;
 // per segment the adjoints follow from the stored final colour, transmittance
-// and depth (C_rest = C_final - C_incl), and are scattered with atomics.
+// and depth (C_rest = C_final - C_incl).
+//
+// Scatter.  Neighbouring rays of a warp mostly walk the same cells (a warp of
+// an 8x4 patch meets ~5 distinct cells per iteration at 1920x1080 and reuses
+// each ~25 times over its walk), so per-lane atomics would hit the same
+// addresses many times.  Each iteration the lanes stage their contributions
+// (SH row, density, the two site positions of the crossing that entered the
+// cell) in shared memory; lanes with the same (previous cell, cell) pair are
+// summed column-wise and the sum is added with one coalesced atomic per
+// value.  A warp whose lanes are spread over many cells scatters per lane.
+constexpr int kMaxGroups = 12;
+
 template <typename AT, int DEG>
-__global__ void __launch_bounds__(kBlock) bwd_kernel(const RenderParams p, const BwdIO io) {
+__global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, const BwdIO io) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int NV = 3 * K;       // SH gradient row
+    constexpr int V = NV + 7;       // + density, position of the cell, position of the previous cell
+    constexpr int SP = 33;          // padded stride: conflict-free column and row access
+    __shared__ float stage_all[kBlock / 32][V * SP];
+    const int lane = threadIdx.x & 31;
+    float *stage = stage_all[threadIdx.x >> 5];
+    const unsigned full = 0xffffffffu;
+
+    // per-lane set-up; no early return: every lane takes part in the
+    // warp-wide scatter until the whole warp is done
     const PixelTask px = pixel_of_thread(p.lc);
-    if (!px.valid) return;
-    const rf_camera &cam = p.lc.cam[px.cam];
-    float3 o, d;
-    camera_ray(cam, px.u, px.v, o, d);
-    const int64_t r = p.lc.ray_begin[px.cam] + (int64_t)px.v * cam.width + px.u;
-    float tmin, tmax;
-    if (!ray_interval(o, d, p.s, cam.t_near, cam.t_far, tmin, tmax)) return;
-
-    const float gC[3] = {io.d_rgb[3 * r], io.d_rgb[3 * r + 1], io.d_rgb[3 * r + 2]};
-    const float gT = io.d_trans ? io.d_trans[r] : 0.f;
-    const float gD = io.d_depth ? io.d_depth[r] : 0.f;
-    if (gC[0] == 0.f && gC[1] == 0.f && gC[2] == 0.f && gT == 0.f && gD == 0.f) return;
-    const float Cf[3] = {io.rgb[3 * r], io.rgb[3 * r + 1], io.rgb[3 * r + 2]};
-    const float Tf = io.trans[r];
-    const float Df = io.depth ? io.depth[r] : 0.f;
-
+    bool live = px.valid;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+    float tmin = 0.f, tmax = 0.f;
+    int64_t r = 0;
+    if (live) {
+        const rf_camera &cam = p.lc.cam[px.cam];
+        camera_ray(cam, px.u, px.v, o, d);
+        r = p.lc.ray_begin[px.cam] + (int64_t)px.v * cam.width + px.u;
+        live = ray_interval(o, d, p.s, cam.t_near, cam.t_far, tmin, tmax);
+    }
+    float gC[3] = {0.f, 0.f, 0.f}, gT = 0.f, gD = 0.f, Cf[3] = {0.f, 0.f, 0.f}, Tf = 0.f, Df = 0.f;
+    if (live) {
+        gC[0] = io.d_rgb[3 * r];
+        gC[1] = io.d_rgb[3 * r + 1];
+        gC[2] = io.d_rgb[3 * r + 2];
+        gT = io.d_trans ? io.d_trans[r] : 0.f;
+        gD = io.d_depth ? io.d_depth[r] : 0.f;
+        live = !(gC[0] == 0.f && gC[1] == 0.f && gC[2] == 0.f && gT == 0.f && gD == 0.f);
+        Cf[0] = io.rgb[3 * r];
+        Cf[1] = io.rgb[3 * r + 1];
+        Cf[2] = io.rgb[3 * r + 2];
+        Tf = io.trans[r];
+        Df = io.depth ? io.depth[r] : 0.f;
+    }
     float Y[16];
     sh_basis<DEG>(d, Y);
-    int i = (int)(p.start_keys[p.lc.cam0 + px.cam] & 0xffffffffull);
+    int i = live ? (int)(p.start_keys[p.lc.cam0 + px.cam] & 0xffffffffull) : 0;
     float t0 = 0.f, T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     int steps = 0;
-    // the crossing that led into the current cell (scattered one step late,
-    // once the t0 adjoint of the next segment is known)
+    // the crossing that entered the current cell: (pa -> i) at pt; its adjoint
+    // padj is complete once the current segment's t0 adjoint is known
     bool pend = false, pend_defines = false;
-    int pa = 0, pb = 0;
+    int pa = -1;
     float3 pxa = make_float3(0.f, 0.f, 0.f), poca = pxa;
     float pt = 0.f, padj = 0.f;
     // the crossing that set the current t0 (t0 <- max(t0, t1))
     int da = -1, db = -1;
     float dt = 0.f;
 
-    while (T > p.eps) {
-        if (steps >= p.max_steps) break;
-        const float4 cell = ldg(p.s.cells + i);
-        Segment g;
-        float3 oc;
-        cell_step<AT, DEG>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc);
-        const float alpha = __fsub_rn(1.f, g.e);
-        const float w = __fmul_rn(T, alpha);
-        const float c[3] = {fmaxf(g.pre[0], 0.f), fmaxf(g.pre[1], 0.f), fmaxf(g.pre[2], 0.f)};
-        const float z = __fmul_rn(0.5f, __fadd_rn(g.a, g.b));
-        C0 = __fmaf_rn(w, c[0], C0);
-        C1 = __fmaf_rn(w, c[1], C1);
-        C2 = __fmaf_rn(w, c[2], C2);
-        D = __fmaf_rn(w, z, D);
-        const float Tn = __fmul_rn(T, g.e);
-        // dL/dsigma_n = delta_n * B, dL/ddelta_n = sigma_n * B with
-        // B = g_C.(T_{n+1} c_n - C_rest) - g_T T_final + g_D (T_{n+1} z_n - D_rest)
-        const float B = gC[0] * (Tn * c[0] - (Cf[0] - C0)) + gC[1] * (Tn * c[1] - (Cf[1] - C1)) +
-                        gC[2] * (Tn * c[2] - (Cf[2] - C2)) - gT * Tf + gD * (Tn * z - (Df - D));
-        if (io.g_density) atomicAdd(io.g_density + i, g.delta * B);
-        if (io.g_sh) {
-            const float cb[3] = {g.pre[0] > 0.f ? gC[0] * w : 0.f, g.pre[1] > 0.f ? gC[1] * w : 0.f,
-                                 g.pre[2] > 0.f ? gC[2] * w : 0.f};
-            if (cb[0] != 0.f || cb[1] != 0.f || cb[2] != 0.f) scatter_sh<DEG>(io.g_sh, i, cb, Y, io.sh_vec);
-        }
-        // segment bounds: delta = max(b - a, 0), z = (a + b)/2,
-        // a = max(t0, t_min), b = min(t1, t_max)
-        const float dbar = g.sigma * B;
-        float abar = 0.5f * gD * w, bbar = abar;
-        if (g.b > g.a) {
-            bbar += dbar;
-            abar -= dbar;
-        }
-        const float t1bar = g.t1 < tmax ? bbar : 0.f;
-        const float t0bar = t0 > tmin ? abar : 0.f;
-        const float3 xi = make_float3(cell.x, cell.y, cell.z);
-        if (pend) {
-            if (pend_defines) {
-                padj += t0bar;
-            } else if (da >= 0 && t0bar != 0.f) {
-                const float4 ca = ldg(p.s.cells + da), cbb = ldg(p.s.cells + db);
-                const float3 xa = make_float3(ca.x, ca.y, ca.z);
-                scatter_crossing(io.g_pos, da, xa,
-                                 make_float3(__fsub_rn(o.x, xa.x), __fsub_rn(o.y, xa.y), __fsub_rn(o.z, xa.z)),
-                                 db, make_float3(cbb.x, cbb.y, cbb.z), dt, d, t0bar);
+    while (__any_sync(full, live)) {
+        // stop tests of Alg. 1 (before the step); a crossing still pending
+        // (T fell to eps right after it) is scattered by this lane alone
+        if (live && (!(T > p.eps) || steps >= p.max_steps)) {
+            live = false;
+            if (pend && padj != 0.f && io.g_pos) {
+                const CellHdr cb = load_cell(p.s, i);
+                const float3 xb = make_float3(cb.x, cb.y, cb.z);
+                const float nx = xb.x - pxa.x, ny = xb.y - pxa.y, nz = xb.z - pxa.z;
+                const float s_ = padj / (nx * d.x + ny * d.y + nz * d.z);
+                const float qx = poca.x + pt * d.x, qy = poca.y + pt * d.y, qz = poca.z + pt * d.z;
+                atomicAdd(io.g_pos + 3 * (int64_t)pa + 0, s_ * qx);
+                atomicAdd(io.g_pos + 3 * (int64_t)pa + 1, s_ * qy);
+                atomicAdd(io.g_pos + 3 * (int64_t)pa + 2, s_ * qz);
+                atomicAdd(io.g_pos + 3 * (int64_t)i + 0, s_ * (nx - qx));
+                atomicAdd(io.g_pos + 3 * (int64_t)i + 1, s_ * (ny - qy));
+                atomicAdd(io.g_pos + 3 * (int64_t)i + 2, s_ * (nz - qz));
             }
-            scatter_crossing(io.g_pos, pa, pxa, poca, i, xi, pt, d, padj);
         }
-        pend = g.next >= 0;
-        pa = i;
-        pb = g.next;
-        pxa = xi;
-        poca = oc;
-        pt = g.t1;
-        padj = t1bar;
-        pend_defines = g.t1 >= t0;
-        if (pend && pend_defines) {
-            da = i;
-            db = g.next;
-            dt = g.t1;
+        float sig_bar = 0.f, cb[3] = {0.f, 0.f, 0.f};
+        float gpos_i[3] = {0.f, 0.f, 0.f}, gpos_a[3] = {0.f, 0.f, 0.f};
+        int key_prev = -1;
+        Segment g;
+        CellHdr cell;
+        float3 oc = make_float3(0.f, 0.f, 0.f);
+        if (live) {
+            cell = load_cell(p.s, i);
+            cell_step<AT, DEG>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc);
+            const float alpha = __fsub_rn(1.f, g.e);
+            const float w = __fmul_rn(T, alpha);
+            const float c[3] = {fmaxf(g.pre[0], 0.f), fmaxf(g.pre[1], 0.f), fmaxf(g.pre[2], 0.f)};
+            const float z = __fmul_rn(0.5f, __fadd_rn(g.a, g.b));
+            C0 = __fmaf_rn(w, c[0], C0);
+            C1 = __fmaf_rn(w, c[1], C1);
+            C2 = __fmaf_rn(w, c[2], C2);
+            D = __fmaf_rn(w, z, D);
+            const float Tn = __fmul_rn(T, g.e);
+            // dL/dsigma_n = delta_n * B, dL/ddelta_n = sigma_n * B with
+            // B = g_C.(T_{n+1} c_n - C_rest) - g_T T_final + g_D (T_{n+1} z_n - D_rest)
+            const float B = gC[0] * (Tn * c[0] - (Cf[0] - C0)) + gC[1] * (Tn * c[1] - (Cf[1] - C1)) +
+                            gC[2] * (Tn * c[2] - (Cf[2] - C2)) - gT * Tf + gD * (Tn * z - (Df - D));
+            sig_bar = io.g_density ? g.delta * B : 0.f;
+            if (io.g_sh) {
+                cb[0] = g.pre[0] > 0.f ? gC[0] * w : 0.f;
+                cb[1] = g.pre[1] > 0.f ? gC[1] * w : 0.f;
+                cb[2] = g.pre[2] > 0.f ? gC[2] * w : 0.f;
+            }
+            // segment bounds: delta = max(b - a, 0), z = (a + b)/2,
+            // a = max(t0, t_min), b = min(t1, t_max)
+            const float dbar = g.sigma * B;
+            float abar = 0.5f * gD * w, bbar = abar;
+            if (g.b > g.a) {
+                bbar += dbar;
+                abar -= dbar;
+            }
+            const float t1bar = g.t1 < tmax ? bbar : 0.f;
+            const float t0bar = t0 > tmin ? abar : 0.f;
+            if (pend) {
+                if (pend_defines) {
+                    padj += t0bar;
+                } else if (da >= 0 && t0bar != 0.f && io.g_pos) {
+                    // t0 was set by an earlier crossing (floating-point tie)
+                    const CellHdr ca = load_cell(p.s, da), cbh = load_cell(p.s, db);
+                    const float nx = cbh.x - ca.x, ny = cbh.y - ca.y, nz = cbh.z - ca.z;
+                    const float s_ = t0bar / (nx * d.x + ny * d.y + nz * d.z);
+                    const float qx = (o.x - ca.x) + dt * d.x, qy = (o.y - ca.y) + dt * d.y,
+                                qz = (o.z - ca.z) + dt * d.z;
+                    atomicAdd(io.g_pos + 3 * (int64_t)da + 0, s_ * qx);
+                    atomicAdd(io.g_pos + 3 * (int64_t)da + 1, s_ * qy);
+                    atomicAdd(io.g_pos + 3 * (int64_t)da + 2, s_ * qz);
+                    atomicAdd(io.g_pos + 3 * (int64_t)db + 0, s_ * (nx - qx));
+                    atomicAdd(io.g_pos + 3 * (int64_t)db + 1, s_ * (ny - qy));
+                    atomicAdd(io.g_pos + 3 * (int64_t)db + 2, s_ * (nz - qz));
+                }
+                // crossing (pa -> i) at pt: dt/dp_i = (p_i - x)/den, dt/dp_a = (x - p_a)/den,
+                // x = o + pt d, den = (p_i - p_a).d
+                if (padj != 0.f && io.g_pos) {
+                    const float nx = cell.x - pxa.x, ny = cell.y - pxa.y, nz = cell.z - pxa.z;
+                    const float s_ = padj / (nx * d.x + ny * d.y + nz * d.z);
+                    const float qx = poca.x + pt * d.x, qy = poca.y + pt * d.y, qz = poca.z + pt * d.z;
+                    gpos_a[0] = s_ * qx;
+                    gpos_a[1] = s_ * qy;
+                    gpos_a[2] = s_ * qz;
+                    gpos_i[0] = s_ * (nx - qx);
+                    gpos_i[1] = s_ * (ny - qy);
+                    gpos_i[2] = s_ * (nz - qz);
+                }
+                key_prev = pa;
+            }
+            // this step's exit becomes the pending crossing
+            pend = g.next >= 0;
+            pa = i;
+            pxa = make_float3(cell.x, cell.y, cell.z);
+            poca = oc;
+            pt = g.t1;
+            padj = t1bar;
+            pend_defines = g.t1 >= t0;
+            if (pend && pend_defines) {
+                da = i;
+                db = g.next;
+                dt = g.t1;
+            }
+            T = Tn;
+            ++steps;
         }
-        T = Tn;
-        ++steps;
-        if (g.next < 0 || !(g.t1 < tmax)) {
-            pend = false;
-            break;
+
+        // ---- warp-wide scatter of this iteration's contributions ----
+        const unsigned long long key =
+            live ? (((unsigned long long)(uint32_t)key_prev << 32) | (uint32_t)i) : ~0ull;
+        const unsigned peers = __match_any_sync(full, key);
+        // lanes that share their (previous cell, cell) with another lane are
+        // summed through shared memory; a lane alone scatters by itself
+        const bool shared_row = live && __popc(peers) > 1;
+        const bool lead = shared_row && lane == __ffs(peers) - 1;
+        unsigned leaders = __ballot_sync(full, lead);
+        const bool grouped = __popc(leaders) <= kMaxGroups;
+        if (live && (!shared_row || !grouped)) {
+            if (io.g_sh && (cb[0] != 0.f || cb[1] != 0.f || cb[2] != 0.f)) scatter_sh<DEG>(io.g_sh, i, cb, Y, io.sh_vec);
+            if (sig_bar != 0.f) atomicAdd(io.g_density + i, sig_bar);
+            if (key_prev >= 0 && io.g_pos) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (gpos_i[a] != 0.f) atomicAdd(io.g_pos + 3 * (int64_t)i + a, gpos_i[a]);
+                    if (gpos_a[a] != 0.f) atomicAdd(io.g_pos + 3 * (int64_t)key_prev + a, gpos_a[a]);
+                }
+            }
         }
-        t0 = g.t1 > t0 ? g.t1 : t0;
-        i = g.next;
-    }
-    // stopped by T <= eps or the step cap right after a crossing
-    if (pend && padj != 0.f) {
-        const float4 cb = ldg(p.s.cells + pb);
-        scatter_crossing(io.g_pos, pa, pxa, poca, pb, make_float3(cb.x, cb.y, cb.z), pt, d, padj);
+        if (grouped && leaders) {
+            if (shared_row) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) stage[q * SP + lane] = cb[q % 3] * Y[q / 3];
+                stage[NV * SP + lane] = sig_bar;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    stage[(NV + 1 + a) * SP + lane] = gpos_i[a];
+                    stage[(NV + 4 + a) * SP + lane] = gpos_a[a];
+                }
+            }
+            __syncwarp();
+            const int c0 = lane, c1 = lane + 32;  // the two value columns this lane sums
+            while (leaders) {
+                const int L = __ffs(leaders) - 1;
+                leaders &= leaders - 1;
+                const unsigned m = __shfl_sync(full, peers, L);
+                const int cell_i = __shfl_sync(full, i, L);
+                const int cell_a = __shfl_sync(full, key_prev, L);
+                float s0 = 0.f, s1 = 0.f;
+                if (c0 < V) {  // a lane only reads the columns that exist (V may be < 32)
+                    for (unsigned mm = m; mm; mm &= mm - 1) {
+                        const int k = __ffs(mm) - 1;
+                        s0 += stage[c0 * SP + k];
+                        if (c1 < V) s1 += stage[c1 * SP + k];
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int col = h ? c1 : c0;
+                    const float sum = h ? s1 : s0;
+                    if (col < V && sum != 0.f) {
+                        if (col < NV) atomicAdd(io.g_sh + (size_t)cell_i * NV + col, sum);
+                        else if (col == NV) atomicAdd(io.g_density + cell_i, sum);
+                        else if (col < NV + 4) atomicAdd(io.g_pos + 3 * (int64_t)cell_i + (col - NV - 1), sum);
+                        else if (cell_a >= 0) atomicAdd(io.g_pos + 3 * (int64_t)cell_a + (col - NV - 4), sum);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+
+        if (live) {
+            if (g.next < 0 || !(g.t1 < tmax)) {
+                live = false;  // nothing pending: the exit lies at or beyond t_max
+            } else {
+                t0 = g.t1 > t0 ? g.t1 : t0;
+                i = g.next;
+            }
+        }
     }
 }
 
@@ -297,6 +411,30 @@ static rf_status common_checks(const rf_scene *s, const rf_camera *cams, int32_t
     for (int c = 0; c < n_cams; ++c) rays += (int64_t)cams[c].width * cams[c].height;
     if (rays >= (1ll << 40)) return fail(RF_ERR_INVALID_ARG, "too many rays");
     return check_opts(opts, eps, max_steps);
+}
+
+// Forward render of n <= kMaxCamsPerLaunch cameras whose outputs start at the
+// given ray offsets (the serving pool), start cells in keys[0..n).
+rf_status launch_fwd_batch(const rf_scene *s, const rf_camera *cams, const int64_t *ray_offsets, int n,
+                           float eps, int32_t max_steps, float *rgb, float *trans, float *depth,
+                           unsigned long long *keys, cudaStream_t st) {
+    if (n < 1 || n > kMaxCamsPerLaunch) return fail(RF_ERR_INVALID_ARG, "batch of %d cameras", n);
+    RenderParams p;
+    memset(&p, 0, sizeof p);
+    p.s = scene_dev(s);
+    p.start_keys = keys;
+    p.eps = eps;
+    p.max_steps = max_steps;
+    rf_status rc = launch_nearest_sites(s, cams, n, keys, st);
+    if (rc != RF_OK) return rc;
+    const int64_t tiles = make_launch_cams(cams, 0, n, 0, &p.lc);
+    for (int c = 0; c < n; ++c) p.lc.ray_begin[c] = ray_offsets[c];
+    FwdOut out = {rgb, trans, depth, nullptr, nullptr, nullptr, 0};
+    dispatch(s->attr_dtype, s->sh_degree, [&]<typename AT, int DEG>() {
+        launch_fwd<AT, DEG>(false, tiles, p, out, st);
+    });
+    RF_CUDA(cudaGetLastError());
+    return RF_OK;
 }
 
 }  // namespace rf

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "rf_host.h"
 
@@ -29,8 +30,9 @@ rf_status cuda_fail(cudaError_t e, const char *what) {
 SceneDev scene_dev(const rf_scene *s) {
     SceneDev d;
     d.cells = s->cells;
-    d.off = s->off;
+    d.ends = s->off + 1;
     d.faces = s->faces;
+    d.sh_v8 = s->sh_v8;
     d.density = s->density;
     d.sh = s->sh;
     for (int a = 0; a < 3; ++a) {
@@ -119,53 +121,66 @@ __global__ void validate_edges_kernel(const int32_t *__restrict__ off,
     }
 }
 
-// One thread per directed edge: face record u = 2 (p_j - p_i)/|p_j - p_i|^2.
-// The owner i of edge f is found by binary search over the offsets.
-__global__ void pack_faces_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ idx,
-                                  const float *__restrict__ pos, int64_t n, int64_t e,
-                                  float4 *__restrict__ faces) {
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= e) return;
-    int64_t lo = 0, hi = n - 1;  // largest i with off[i] <= f
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (__ldg(off + mid) <= f) lo = mid; else hi = mid - 1;
-    }
-    const int64_t i = lo;
-    const int32_t j = idx[f];
+__device__ __forceinline__ float4 face_record(const float *__restrict__ pos, int64_t i, int32_t j) {
     const float nx = __fsub_rn(pos[3 * (int64_t)j], pos[3 * i]);
     const float ny = __fsub_rn(pos[3 * (int64_t)j + 1], pos[3 * i + 1]);
     const float nz = __fsub_rn(pos[3 * (int64_t)j + 2], pos[3 * i + 2]);
     const float nn = __fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz)));
     const float s = __fdiv_rn(2.f, nn);
-    faces[f] = make_float4(__fmul_rn(nx, s), __fmul_rn(ny, s), __fmul_rn(nz, s), __int_as_float(j));
+    return make_float4(__fmul_rn(nx, s), __fmul_rn(ny, s), __fmul_rn(nz, s), __int_as_float(j));
 }
 
-// Re-pack after the sites moved: neighbour ids come from the existing records.
-__global__ void repack_faces_kernel(const int32_t *__restrict__ off, const float *__restrict__ pos,
-                                    int64_t n, int64_t e, float4 *__restrict__ faces) {
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= e) return;
+// Largest i with off[i] <= f (off monotone, off[0] = 0 <= f).
+__device__ __forceinline__ int64_t owner_of(const int32_t *__restrict__ off, int64_t n, int64_t f) {
     int64_t lo = 0, hi = n - 1;
     while (lo < hi) {
         const int64_t mid = (lo + hi + 1) >> 1;
         if (__ldg(off + mid) <= f) lo = mid; else hi = mid - 1;
     }
-    const int64_t i = lo;
-    const int32_t j = __float_as_int(faces[f].w);
-    const float nx = __fsub_rn(pos[3 * (int64_t)j], pos[3 * i]);
-    const float ny = __fsub_rn(pos[3 * (int64_t)j + 1], pos[3 * i + 1]);
-    const float nz = __fsub_rn(pos[3 * (int64_t)j + 2], pos[3 * i + 2]);
-    const float nn = __fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz)));
-    const float s = __fdiv_rn(2.f, nn);
-    faces[f] = make_float4(__fmul_rn(nx, s), __fmul_rn(ny, s), __fmul_rn(nz, s), __int_as_float(j));
+    return lo;
 }
 
-__global__ void pack_cells_kernel(const int32_t *__restrict__ off, const float *__restrict__ pos,
-                                  int64_t n, float4 *__restrict__ cells) {
+// One thread per caller edge f of cell i: face record u = 2 (p_j - p_i)/|p_j - p_i|^2
+// at slot poff[i] + (f - off[i]) of the padded list.
+__global__ void pack_faces_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ poff,
+                                  const int32_t *__restrict__ idx, const float *__restrict__ pos,
+                                  int64_t n, int64_t e, float4 *__restrict__ faces) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= e) return;
+    const int64_t i = owner_of(off, n, f);
+    faces[(int64_t)poff[i] + (f - off[i])] = face_record(pos, i, idx[f]);
+}
+
+// Re-pack after the sites moved: neighbour ids come from the existing records.
+__global__ void repack_faces_kernel(const int32_t *__restrict__ poff, const float *__restrict__ pos,
+                                    int64_t n, int64_t slots, float4 *__restrict__ faces) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= slots) return;
+    const int32_t j = __float_as_int(faces[f].w);
+    if (j < 0) return;  // padding
+    faces[f] = face_record(pos, owner_of(poff, n, f), j);
+}
+
+// Headers and list padding: cell i owns slots [poff[i], poff[i+1]); the caller's
+// count is off[i+1] - off[i]; a slot beyond it is padding {0, 0, 0, -1}.
+__global__ void pack_cells_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ poff,
+                                  const float *__restrict__ pos, int64_t n, float4 *__restrict__ cells,
+                                  float4 *__restrict__ faces) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    cells[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], __int_as_float(off[i]));
+    const int32_t b = poff[i], e = poff[i + 1];
+    cells[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], __int_as_float(b));
+    if (off) {
+        for (int32_t f = b + (off[i + 1] - off[i]); f < e; ++f)
+            faces[f] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    }
+}
+
+__global__ void update_cells_kernel(const float *__restrict__ pos, int64_t n, float4 *__restrict__ cells) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 h = cells[i];
+    cells[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], h.w);
 }
 
 // Order-preserving map of floats to signed ints for atomic min / max.
@@ -276,25 +291,12 @@ static rf_status check_attr_ptrs(const void *density, const void *sh, int32_t dt
     return RF_OK;
 }
 
-static rf_status do_pack(rf_scene *s, const float *pos, const int32_t *adj_idx, cudaStream_t st) {
-    const int threads = 256;
-    if (s->n_edges > 0) {
-        pack_faces_kernel<<<(unsigned)((s->n_edges + threads - 1) / threads), threads, 0, st>>>(
-            s->off, adj_idx, pos, s->n_sites, s->n_edges, s->faces);
-        RF_CUDA(cudaGetLastError());
-    }
-    pack_cells_kernel<<<(unsigned)((s->n_sites + threads - 1) / threads), threads, 0, st>>>(
-        s->off, pos, s->n_sites, s->cells);
-    RF_CUDA(cudaGetLastError());
-    return RF_OK;
-}
-
 RF_API rf_status rf_scene_create(const rf_scene_desc *desc, void *stream, rf_scene **out) {
     if (!desc || !out) return fail(RF_ERR_INVALID_ARG, "desc and out must not be NULL");
     *out = nullptr;
     const int64_t n = desc->n_sites, e = desc->n_edges;
-    if (n < 1 || n >= (1ll << 31) || e < 0 || e >= (1ll << 31))
-        return fail(RF_ERR_INVALID_ARG, "n_sites must be in [1, 2^31) and n_edges in [0, 2^31)");
+    if (n < 1 || n >= (1ll << 30) || e < 0 || e >= (1ll << 30))
+        return fail(RF_ERR_INVALID_ARG, "n_sites must be in [1, 2^30) and n_edges in [0, 2^30)");
     if (!desc->pos || !desc->adj_off || (e > 0 && !desc->adj_idx))
         return fail(RF_ERR_INVALID_ARG, "pos, adj_off and adj_idx must be device pointers");
     if (desc->sh_degree < 0 || desc->sh_degree > RF_MAX_SH_DEGREE)
@@ -310,6 +312,7 @@ RF_API rf_status rf_scene_create(const rf_scene_desc *desc, void *stream, rf_sce
     s->sh = desc->sh;
     s->sh_degree = desc->sh_degree;
     s->attr_dtype = desc->attr_dtype;
+    s->sh_v8 = ((uintptr_t)desc->sh & 31) == 0;
     cudaGetDevice(&s->device);
 #define RF_TRY_ALLOC(ptr, nbytes_)                                 \
     do {                                                           \
@@ -320,12 +323,9 @@ RF_API rf_status rf_scene_create(const rf_scene_desc *desc, void *stream, rf_sce
         }                                                          \
         s->bytes += (nbytes_);                                     \
     } while (0)
-    RF_TRY_ALLOC(s->cells, sizeof(float4) * n);
     RF_TRY_ALLOC(s->off, sizeof(int32_t) * (n + 1));
-    RF_TRY_ALLOC(s->faces, sizeof(float4) * (e > 0 ? e : 1));
     RF_TRY_ALLOC(s->start_keys, sizeof(unsigned long long) * kMaxCamsPerLaunch);
     RF_TRY_ALLOC(s->flags, sizeof(int32_t) * 8);
-#undef RF_TRY_ALLOC
 
     auto bail = [&](rf_status r) {
         free_scene(s);
@@ -353,8 +353,36 @@ RF_API rf_status rf_scene_create(const rf_scene_desc *desc, void *stream, rf_sce
         return bail(fail(RF_ERR_BAD_SCENE,
                          "adjacency invalid: %d out-of-range/self, %d asymmetric, %d zero-length edges",
                          flags[1], flags[2], flags[3]));
-    rc = do_pack(s, desc->pos, desc->adj_idx, st);
-    if (rc != RF_OK) return bail(rc);
+
+    // padded lists: each cell's count rounded up to even, so every list starts
+    // at an even slot and faces can be read in 32-byte pairs
+    std::vector<int32_t> off_h(n + 1), poff_h(n + 1);
+    if ((ce = cudaMemcpyAsync(off_h.data(), s->off, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
+                              st)) != cudaSuccess ||
+        (ce = cudaStreamSynchronize(st)) != cudaSuccess)
+        return bail(cuda_fail(ce, "read offsets"));
+    int64_t acc = 0;
+    poff_h[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t c = off_h[i + 1] - off_h[i];
+        acc += c + (c & 1);
+        poff_h[i + 1] = (int32_t)acc;
+    }
+    s->n_slots = acc;
+    RF_TRY_ALLOC(s->faces, sizeof(float4) * (acc > 0 ? acc : 2));
+    RF_TRY_ALLOC(s->cells, sizeof(float4) * n);
+#undef RF_TRY_ALLOC
+    if ((ce = cudaMemcpyAsync(s->off, poff_h.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
+                              st)) != cudaSuccess)
+        return bail(cuda_fail(ce, "upload padded offsets"));
+    if (e > 0) {
+        pack_faces_kernel<<<(unsigned)((e + threads - 1) / threads), threads, 0, st>>>(
+            desc->adj_off, s->off, desc->adj_idx, desc->pos, n, e, s->faces);
+        if ((ce = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(ce, "pack faces"));
+    }
+    pack_cells_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
+        desc->adj_off, s->off, desc->pos, n, s->cells, s->faces);
+    if ((ce = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(ce, "pack cells"));
 
     bool box_ok = true;
     for (int a = 0; a < 3; ++a) box_ok = box_ok && desc->aabb_min[a] <= desc->aabb_max[a];
@@ -389,21 +417,22 @@ RF_API rf_status rf_scene_set_attributes(rf_scene *s, const void *density, const
     s->density = density;
     s->sh = sh;
     s->attr_dtype = attr_dtype;
+    s->sh_v8 = ((uintptr_t)sh & 31) == 0;
     return RF_OK;
 }
 
 RF_API rf_status rf_scene_update_positions(rf_scene *s, const float *pos, void *stream) {
     if (!s || !pos) return fail(RF_ERR_INVALID_ARG, "scene and pos must not be NULL");
-    // the face records need the neighbour ids, which the packed faces hold
+    // the face records hold the neighbour ids; only the geometry is recomputed
     const int threads = 256;
     cudaStream_t st = (cudaStream_t)stream;
-    if (s->n_edges > 0) {
-        repack_faces_kernel<<<(unsigned)((s->n_edges + threads - 1) / threads), threads, 0, st>>>(
-            s->off, pos, s->n_sites, s->n_edges, s->faces);
+    if (s->n_slots > 0) {
+        repack_faces_kernel<<<(unsigned)((s->n_slots + threads - 1) / threads), threads, 0, st>>>(
+            s->off, pos, s->n_sites, s->n_slots, s->faces);
         RF_CUDA(cudaGetLastError());
     }
-    pack_cells_kernel<<<(unsigned)((s->n_sites + threads - 1) / threads), threads, 0, st>>>(
-        s->off, pos, s->n_sites, s->cells);
+    update_cells_kernel<<<(unsigned)((s->n_sites + threads - 1) / threads), threads, 0, st>>>(
+        pos, s->n_sites, s->cells);
     RF_CUDA(cudaGetLastError());
     return RF_OK;
 }

@@ -52,6 +52,21 @@ class rf_render_opts(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
 
 
+class rf_serve_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("eps", ctypes.c_float), ("max_steps", ctypes.c_int32)]
+
+
+class rf_serve_metrics(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("rays_done", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mrays_s", ctypes.c_double), ("mean_batch", ctypes.c_double),
+                ("max_busy_streams", ctypes.c_int32), ("inflight", ctypes.c_int32)]
+
+
 class RFError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"rf error {code}: {msg}")
@@ -81,6 +96,15 @@ SIGNATURES = {
     "rf_trace_cells": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.POINTER(rf_render_opts),
                             ctypes.c_int32, _P, _P, _P]),
     "rf_mse_grad": (_S, [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
+    "rf_serve_create": (_S, [_P, ctypes.POINTER(rf_serve_config), ctypes.POINTER(_P)]),
+    "rf_serve_submit": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.POINTER(ctypes.c_uint64)]),
+    "rf_serve_poll": (_S, [_P, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_double)]),
+    "rf_serve_wait": (_S, [_P, ctypes.c_uint64, ctypes.c_int32, _P,
+                           ctypes.POINTER(ctypes.c_double)]),
+    "rf_serve_stats": (_S, [_P, ctypes.POINTER(rf_serve_metrics)]),
+    "rf_serve_reset_stats": (_S, [_P]),
+    "rf_serve_destroy": (_S, [_P]),
     "rf_render_fwd_noalloc": (_S, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
                                    ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(rf_camera), ctypes.c_int32,

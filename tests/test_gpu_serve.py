@@ -1,0 +1,117 @@
+"""Continuous-batching server: admission by memory, overlap of batches on the
+device, and identical images alone and in a mix of concurrent requests."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2502_01157_gb300 import rf
+from paper_2502_01157_gb300 import scenes as S
+from paper_2502_01157_gb300.serve import Server, run_open_loop
+from tests.helpers import camera_at, random_scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def foam():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    sc = random_scene(4000, 3, 77)
+    rng = np.random.default_rng(78)
+    sc.sh[:, 1:, :] = rng.normal(0, 0.3, sc.sh[:, 1:, :].shape).astype(np.float32)
+    f = rf.Foam.from_scene(sc, attr_dtype=torch.bfloat16)
+    yield f
+    f.close()
+
+
+def _cams(n, seed):
+    rng = np.random.default_rng(seed)
+    sizes = [(32, 24), (64, 48), (128, 72), (192, 108)]
+    out = []
+    for k in range(n):
+        w, h = sizes[rng.integers(0, len(sizes))]
+        v = rng.normal(size=3)
+        out.append(S.pinhole(w, h, 60.0, c2w=S.look_at(2.4 * v / np.linalg.norm(v))))
+    return out
+
+
+def _image(foam, cam):
+    out = foam.render([cam])
+    torch.cuda.synchronize()
+    return out["rgb"].cpu().numpy()
+
+
+def test_result_is_the_same_alone_and_in_the_mix(foam):
+    target = S.pinhole(96, 64, 60.0, c2w=S.look_at((1.5, -1.8, 0.9)))
+    ref = _image(foam, target)
+    srv = Server(foam, mem_budget_bytes=64 << 20, max_inflight=64, n_streams=3, max_batch=4)
+    alone = np.zeros((target.n_rays, 3), np.float32)
+    srv.wait(srv.submit(target), out=alone)
+    np.testing.assert_array_equal(alone, ref)
+    # the same request again, submitted in the middle of a burst of others
+    others = _cams(40, 1)
+    ids = [srv.submit(c) for c in others[:20]]
+    mine = srv.submit(target)
+    ids += [srv.submit(c) for c in others[20:]]
+    mixed = np.zeros_like(alone)
+    srv.wait(mine, out=mixed)
+    for rid, cam in zip(ids, others):
+        if rid is not None:
+            img = np.zeros((cam.n_rays, 3), np.float32)
+            srv.wait(rid, out=img)
+            np.testing.assert_array_equal(img, _image(foam, cam))
+    np.testing.assert_array_equal(mixed, ref)
+    st = srv.stats()
+    assert st["mean_batch"] > 1.0, st          # requests were batched together
+    assert st["max_busy_streams"] > 1, st      # batches overlapped on the device
+    srv.close()
+
+
+def test_admission_by_memory(foam):
+    cam = S.pinhole(40, 30, 60.0, c2w=S.look_at((2.0, 1.0, 0.5)))
+    srv = Server(foam, mem_budget_bytes=2 * cam.n_rays * 20, max_inflight=8, n_streams=1, max_batch=1)
+    a = srv.submit(cam)
+    b = srv.submit(cam)
+    assert a is not None and b is not None
+    assert srv.submit(cam) is None            # no memory left: rejected at once
+    srv.wait(a)                               # collecting a frees its memory
+    c = srv.submit(cam)
+    assert c is not None
+    srv.wait(b)
+    srv.wait(c)
+    big = S.pinhole(400, 300, 60.0, c2w=S.look_at((2.0, 1.0, 0.5)))
+    with pytest.raises(rf.RFError) as e:
+        srv.submit(big)                       # can never fit
+    assert e.value.code == 1
+    assert srv.stats()["rejected"] >= 2
+    srv.close()
+
+
+def test_slot_limit_and_invalid_requests(foam):
+    cam = S.pinhole(16, 16, 60.0, c2w=S.look_at((2.0, 0.0, 0.0)))
+    srv = Server(foam, mem_budget_bytes=16 << 20, max_inflight=2, n_streams=2, max_batch=2)
+    ids = [srv.submit(cam), srv.submit(cam)]
+    assert srv.submit(cam) is None
+    bad = S.pinhole(16, 16, 60.0, c2w=S.look_at((2.0, 0.0, 0.0)))
+    bad.c2w[1, 3] = np.inf
+    with pytest.raises(rf.RFError):
+        srv.submit(bad)
+    for rid in ids:
+        srv.wait(rid)
+    with pytest.raises(rf.RFError) as e:
+        srv.poll(ids[0])                      # already collected
+    assert e.value.code == 8
+    srv.close()
+
+
+def test_open_loop_poisson_stream(foam):
+    cams = _cams(300, 5)
+    arrivals = S.poisson_arrivals(600.0, len(cams), 9)
+    srv = Server(foam, mem_budget_bytes=256 << 20, max_inflight=128, n_streams=4, max_batch=8)
+    st = run_open_loop(srv, cams, arrivals)
+    assert st["completed"] + st["rejected_open_loop"] == len(cams)
+    assert st["completed"] > 0.9 * len(cams)
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+    print("serve", {k: st[k] for k in ("completed", "rejected_open_loop", "p50_ms", "p99_ms",
+                                         "mrays_s", "mean_batch", "max_busy_streams")})
+    srv.close()
