@@ -96,7 +96,10 @@ __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 
 // Map a block to (camera, tile) and a thread to a pixel: warp w of the block
 // covers an 8x4 patch of the 16x8 tile, so the 32 rays of a warp are
-// neighbours on the image and walk through mostly the same cells.
+// neighbours on the image and walk through mostly the same cells.  Lanes are
+// laid out in Z-order inside the patch (lanes 4q..4q+3 form a 2x2 quad, 8q..8q+7
+// a 4x2 block): the L1 serves a load in units of consecutive lanes, and compact
+// units meet fewer distinct cells than an 8x1 row.
 struct PixelTask {
     int cam, u, v;
     bool valid;
@@ -113,8 +116,10 @@ __device__ __forceinline__ PixelTask pixel_of_thread(const LaunchCams &lc) {
     const int ty = lt / lc.tiles_x[c];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     t.cam = c;
-    t.u = tx * kTileW + (w & 1) * 8 + (l & 7);
-    t.v = ty * kTileH + (w >> 1) * 4 + (l >> 3);
+    const int lx = (l & 1) | ((l >> 1) & 2) | ((l >> 2) & 4);  // bits 0, 2, 4 of the lane
+    const int ly = ((l >> 1) & 1) | ((l >> 2) & 2);            // bits 1, 3
+    t.u = tx * kTileW + (w & 1) * 8 + lx;
+    t.v = ty * kTileH + (w >> 1) * 4 + ly;
     t.valid = t.u < lc.cam[c].width && t.v < lc.cam[c].height;
     return t;
 }
