@@ -15,6 +15,7 @@ function follows the paper's statement of the method:
 * :func:`render_bwd`   -- reverse-mode gradient of the rendered outputs; sites
   receive gradient only through segment widths (Sec. 3.1).
 * :func:`sh_basis`     -- real spherical harmonics of degree <= 3 (Sec. 3.4).
+* :func:`render_quantile` -- the quantile loss of Eq. (6) per ray (Sec. 3.3).
 """
 from __future__ import annotations
 
@@ -76,7 +77,11 @@ def lib():
             L.orc_render.restype = ctypes.c_int
             L.orc_render_bwd.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int, _d,
                                          _d, ctypes.c_int64, _i64, ctypes.c_double, ctypes.c_int,
-                                         _d, _d, _d, _d, _d, _d, ctypes.c_int]
+                                         _d, _d, _d, _d, _d, _d, _d, ctypes.c_int]
+            L.orc_render_quantile.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int,
+                                              _d, _d, ctypes.c_int64, _i64, ctypes.c_double,
+                                              ctypes.c_int, _d, ctypes.c_int]
+            L.orc_render_quantile.restype = ctypes.c_int
             L.orc_render_bwd.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = ctypes.c_int
@@ -184,10 +189,30 @@ def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
     return out
 
 
+def render_quantile(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
+                    threads: int = 0) -> np.ndarray:
+    """Quantile loss of Eq. (6) per ray: E|W^-1(u1) - W^-1(u2)|, u1, u2 ~ U[0,1],
+    W^-1 the quantile function of the ray's normalised weight distribution."""
+    S = _SceneF64(scene)
+    c = _cam(cam)
+    n_all = int(c[16]) * int(c[17])
+    px = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
+    R = n_all if px is None else len(px)
+    q = np.zeros(R)
+    rc = lib().orc_render_quantile(S.n, _p(S.pos, _d), _p(S.off, _i64), _p(S.adj, _i32),
+                                   _p(S.sigma, _d), _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d),
+                                   R, _p(px, _i64), float(eps), int(max_steps), _p(q, _d),
+                                   int(threads))
+    if rc:
+        raise ValueError("oracle render_quantile: bad arguments")
+    return q
+
+
 def render_bwd(scene, cam, g_rgb, g_trans=None, g_depth=None, pixels=None, eps: float = 1e-4,
-               max_steps: int = 1 << 16, threads: int = 0) -> dict:
+               max_steps: int = 1 << 16, threads: int = 0, g_quantile=None) -> dict:
     """Gradient of sum(g_rgb*rgb) + sum(g_trans*trans) + sum(g_depth*depth)
-    with respect to density [N], SH [N,K,3] and positions [N,3]."""
+    + sum(g_quantile*quantile) with respect to density [N], SH [N,K,3] and
+    positions [N,3]."""
     S = _SceneF64(scene)
     c = _cam(cam)
     n_all = int(c[16]) * int(c[17])
@@ -196,6 +221,7 @@ def render_bwd(scene, cam, g_rgb, g_trans=None, g_depth=None, pixels=None, eps: 
     gr = _f64(g_rgb).reshape(R, 3)
     gt = None if g_trans is None else _f64(g_trans).reshape(R)
     gd = None if g_depth is None else _f64(g_depth).reshape(R)
+    gq = None if g_quantile is None else _f64(g_quantile).reshape(R)
     K = (S.deg + 1) ** 2
     g_sigma = np.zeros(S.n)
     g_sh = np.zeros((S.n, K, 3))
@@ -203,7 +229,7 @@ def render_bwd(scene, cam, g_rgb, g_trans=None, g_depth=None, pixels=None, eps: 
     rc = lib().orc_render_bwd(S.n, _p(S.pos, _d), _p(S.off, _i64), _p(S.adj, _i32),
                               _p(S.sigma, _d), _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d), R,
                               _p(px, _i64), float(eps), int(max_steps), _p(gr, _d), _p(gt, _d),
-                              _p(gd, _d), _p(g_sigma, _d), _p(g_sh, _d), _p(g_pos, _d),
+                              _p(gd, _d), _p(gq, _d), _p(g_sigma, _d), _p(g_sh, _d), _p(g_pos, _d),
                               int(threads))
     if rc:
         raise ValueError("oracle render_bwd: bad arguments")

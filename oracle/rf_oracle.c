@@ -20,7 +20,12 @@
  *     delta), C += T alpha c, T *= (1 - alpha), while T > eps.
  *   - Colour from real spherical harmonics of degree <= 3 in the ray
  *     direction, plus 0.5, clamped at 0 (Sec. 3.4 "Training").
- *   - The gradient of (rgb, transmittance, depth) with respect to density,
+ *   - The quantile loss of Eq. (6): the expected distance between two
+ *     quantiles of the ray's weight distribution, E|W^-1(u1) - W^-1(u2)| with
+ *     u1, u2 ~ U[0,1], which equals 2 * integral F(t)(1 - F(t)) dt for the
+ *     normalised weight CDF F = (1 - T(t)) / (1 - T_final); per segment the
+ *     integral has a closed form (exponential transmittance).
+ *   - The gradient of (rgb, transmittance, depth, quantile loss) with respect to density,
  *     SH coefficients and site positions, by plain reverse-mode
  *     differentiation of the stored segment list; positions receive gradient
  *     only through the segment widths (Sec. 3.1).
@@ -317,6 +322,87 @@ static void render_ray(const scene_t *S, int64_t start, const double *o, const d
     R->steps = steps;
 }
 
+/* a = (1 - e^{-s d}) / s and b = (1 - e^{-2 s d}) / (2 s): the integrals of
+ * T(t)/T_n and (T(t)/T_n)^2 over a segment of width d and density s, with
+ * their partial derivatives in s and d. */
+static void seg_integrals(double s, double d, double *a, double *b, double *da_ds, double *da_dd,
+                          double *db_ds, double *db_dd)
+{
+    const double x = s * d;
+    const double e = exp(-x);
+    if (x < 1e-4) {
+        /* series in x (exact to O(x^4)) */
+        *a = d * (1.0 - x / 2.0 + x * x / 6.0 - x * x * x / 24.0);
+        *b = d * (1.0 - x + 2.0 * x * x / 3.0 - x * x * x / 3.0);
+        *da_ds = -d * d * (0.5 - x / 3.0 + x * x / 8.0 - x * x * x / 30.0);
+        *db_ds = d * d * (-1.0 + 4.0 * x / 3.0 - x * x + 8.0 * x * x * x / 15.0);
+    } else {
+        *a = -expm1(-x) / s;
+        *b = -expm1(-2.0 * x) / (2.0 * s);
+        *da_ds = (x * e + expm1(-x)) / (s * s);
+        *db_ds = (2.0 * x * e * e + expm1(-2.0 * x)) / (2.0 * s * s);
+    }
+    *da_dd = e;
+    *db_dd = e * e;
+}
+
+/* Quantile loss of Eq. (6) for one ray: with F = (1 - T)/(1 - T_f),
+ * 2 * int F (1 - F) dt = 2/(1 - T_f)^2 * sum_n int_seg (1 - T)(T - T_f) dt and
+ * int_seg (1 - T)(T - T_f) = (1 + T_f) T_n a_n - T_n^2 b_n - T_f delta_n. */
+static double quantile_loss(const seglist_t *L, double Tf)
+{
+    const double W = 1.0 - Tf;
+    if (!(W > 0.0)) return 0.0;
+    double S = 0.0;
+    for (int64_t k = 0; k < L->n; ++k) {
+        const seg_t *g = &L->s[k];
+        if (!(g->delta > 0.0)) continue;
+        double a, b, t1, t2, t3, t4;
+        seg_integrals(g->sigma, g->delta, &a, &b, &t1, &t2, &t3, &t4);
+        S += (1.0 + Tf) * g->T * a - g->T * g->T * b - Tf * g->delta;
+    }
+    return 2.0 * S / (W * W);
+}
+
+/* Adjoints of the quantile loss (scaled by gq) with respect to each
+ * segment's density and width, by reverse-mode differentiation of
+ * quantile_loss through T_n = prod_{k<n} e_k and T_f = prod_k e_k. */
+static void quantile_adjoints(const seglist_t *L, double Tf, double gq, double *qsig, double *qdel)
+{
+    const double W = 1.0 - Tf;
+    for (int64_t k = 0; k < L->n; ++k) qsig[k] = qdel[k] = 0.0;
+    if (!(W > 0.0) || gq == 0.0) return;
+    double S = 0.0, dS_dTf = 0.0;
+    for (int64_t k = 0; k < L->n; ++k) {
+        const seg_t *g = &L->s[k];
+        if (!(g->delta > 0.0)) continue;
+        double a, b, t1, t2, t3, t4;
+        seg_integrals(g->sigma, g->delta, &a, &b, &t1, &t2, &t3, &t4);
+        S += (1.0 + Tf) * g->T * a - g->T * g->T * b - Tf * g->delta;
+        dS_dTf += g->T * a - g->delta;
+    }
+    const double c = 2.0 / (W * W);
+    const double Sbar = gq * c;
+    /* L = c(T_f) S(T_f, ...): dc/dT_f = 4 / W^3 */
+    double Tbar = gq * S * 4.0 / (W * W * W) + Sbar * dS_dTf;  /* adjoint of T after the last segment */
+    for (int64_t k = L->n - 1; k >= 0; --k) {
+        const seg_t *g = &L->s[k];
+        double a = g->delta, b = g->delta, da_ds = 0, da_dd = 1, db_ds = 0, db_dd = 1;
+        if (g->delta > 0.0) seg_integrals(g->sigma, g->delta, &a, &b, &da_ds, &da_dd, &db_ds, &db_dd);
+        else a = b = 0.0;
+        const double ebar = Tbar * g->T;   /* T_{k+1} = T_k e_k */
+        const double dI_dT = g->delta > 0.0 ? (1.0 + Tf) * a - 2.0 * g->T * b : 0.0;
+        if (g->delta > 0.0) {
+            qsig[k] = Sbar * ((1.0 + Tf) * g->T * da_ds - g->T * g->T * db_ds);
+            qdel[k] = Sbar * ((1.0 + Tf) * g->T * da_dd - g->T * g->T * db_dd - Tf);
+        }
+        /* e_k = exp(-sigma_k delta_k) */
+        qsig[k] += ebar * (-g->delta * g->e);
+        qdel[k] += ebar * (-g->sigma * g->e);
+        Tbar = Tbar * g->e + Sbar * dI_dT;
+    }
+}
+
 static int setup_scene(scene_t *S, int64_t n, const double *pos, const int64_t *off,
                        const int32_t *adj, const double *sigma, const double *sh, int deg,
                        const double *box)
@@ -377,6 +463,38 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
     return 0;
 }
 
+/* Quantile loss of Eq. (6) per ray (0 for a ray with no weight). */
+int orc_render_quantile(int64_t n_sites, const double *pos, const int64_t *off, const int32_t *adj,
+                        const double *sigma, const double *sh, int sh_degree, const double *box,
+                        const double *cam, int64_t n_rays, const int64_t *pixels, double eps,
+                        int max_steps, double *quantile, int n_threads)
+{
+    scene_t S;
+    if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
+    double o[3], dummy[3];
+    orc_camera_ray(cam, 0, o, dummy);
+    const int64_t start = orc_nearest_site(n_sites, pos, o, NULL);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t r = 0; r < n_rays; ++r) {
+        const int64_t px = pixels ? pixels[r] : r;
+        double ro[3], rd[3], Y[16], tmin, tmax;
+        orc_camera_ray(cam, px, ro, rd);
+        orc_sh_basis(S.deg, rd, Y);
+        quantile[r] = 0.0;
+        if (!ray_interval(ro, rd, box, cam[18], cam[19], &tmin, &tmax)) continue;
+        ray_out_t R;
+        memset(&R, 0, sizeof R);
+        seglist_t L = {NULL, 0, 0};
+        render_ray(&S, start, ro, rd, tmin, tmax, eps, max_steps, -1.0, Y, &R, &L, 0, NULL, NULL);
+        quantile[r] = quantile_loss(&L, R.T);
+        free(L.s);
+    }
+    return 0;
+}
+
 #ifdef _OPENMP
 #define ORC_ATOMIC _Pragma("omp atomic")
 #else
@@ -384,9 +502,10 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
 #endif
 
 /*
- * Gradient of L = g_rgb . rgb + g_trans * T + g_depth * depth for n_rays
- * pixels of one camera, accumulated (+=) into g_sigma [N], g_sh [N,K,3] and
- * g_pos [N,3].  g_trans / g_depth may be NULL (zero).  The forward walk is
+ * Gradient of L = g_rgb . rgb + g_trans * T + g_depth * depth + g_quantile *
+ * quantile for n_rays pixels of one camera, accumulated (+=) into g_sigma
+ * [N], g_sh [N,K,3] and g_pos [N,3].  g_trans / g_depth / g_quantile may be
+ * NULL (zero).  The forward walk is
  * repeated with its segments stored, then differentiated in reverse order.
  */
 int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const int32_t *adj,
@@ -394,7 +513,8 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
                    const double *cam, int64_t n_rays, const int64_t *pixels,
                    double eps, int max_steps,
                    const double *g_rgb, const double *g_trans, const double *g_depth,
-                   double *g_sigma, double *g_sh, double *g_pos, int n_threads)
+                   const double *g_quantile, double *g_sigma, double *g_sh, double *g_pos,
+                   int n_threads)
 {
     scene_t S;
     if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
@@ -420,6 +540,10 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
         const double gC[3] = {g_rgb[3 * r], g_rgb[3 * r + 1], g_rgb[3 * r + 2]};
         const double gT = g_trans ? g_trans[r] : 0.0;
         const double gD = g_depth ? g_depth[r] : 0.0;
+        const double gQ = g_quantile ? g_quantile[r] : 0.0;
+        double *qsig = (double *)calloc((size_t)(L.n > 0 ? 2 * L.n : 2), sizeof(double));
+        double *qdel = qsig + (L.n > 0 ? L.n : 1);
+        quantile_adjoints(&L, R.T, gQ, qsig, qdel);
         double Tbar = gT;       /* adjoint of the transmittance after segment k */
         double t0bar_next = 0.0;  /* adjoint of t0 of segment k+1 */
         for (int64_t k = L.n - 1; k >= 0; --k) {
@@ -431,8 +555,8 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
             /* T_{k+1} = T_k e_k;  C += T_k (1 - e_k) c_k;  D += T_k (1 - e_k) z_k */
             const double ebar = Tbar * s->T - wbar * s->T;
             Tbar = Tbar * s->e + wbar * (1.0 - s->e);
-            const double sigbar = ebar * (-s->delta * s->e);
-            const double dbar = ebar * (-s->sigma * s->e);
+            const double sigbar = ebar * (-s->delta * s->e) + qsig[k];
+            const double dbar = ebar * (-s->sigma * s->e) + qdel[k];
             const double zbar = gD * w;
             double abar = 0.5 * zbar, bbar = 0.5 * zbar;
             if (s->b > s->a) { bbar += dbar; abar -= dbar; }
@@ -474,6 +598,7 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
                 }
             }
         }
+        free(qsig);
         free(L.s);
     }
     return 0;
