@@ -446,6 +446,30 @@ def main():
             res[f"fwdbwd_{name}_mrays_s"] = R / (b.elapsed_time(c) / args.steps * 1e-3) / 1e6
         foam.set_attributes(torch.from_numpy(scene.density).to(dev),
                             torch.from_numpy(scene.sh).to(dev))
+        # training step with the quantile regulariser of Eq. 6 fused into the walks:
+        # L = MSE + lambda * mean quantile loss (lambda = 0.01)
+        qout = dict(out, quantile=torch.empty(R, device=dev), quantile_aux=torch.empty(R, 5, device=dev))
+        d_q = torch.full((R,), 0.01 / R, device=dev)
+
+        def qstep():
+            foam.render([cam], out=qout)
+            d_rgb, _ = rf.mse_grad(qout["rgb"], target, scale, loss)
+            foam.backward([cam], qout, d_rgb, grads=grads, d_quantile=d_q)
+
+        for _ in range(2):
+            qstep()
+        barrier()
+        a, b, c = ev(), ev(), ev()
+        a.record()
+        for _ in range(args.steps):
+            foam.render([cam], out=qout)
+        b.record()
+        for _ in range(args.steps):
+            qstep()
+        c.record()
+        barrier()
+        res["fwd_quantile_fp32_mrays_s"] = R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
+        res["fwdbwd_quantile_fp32_mrays_s"] = R / (b.elapsed_time(c) / args.steps * 1e-3) / 1e6
 
     mixture = None
     if mix_scene is not None:

@@ -199,6 +199,61 @@ RF_API rf_status rf_render_bwd(rf_scene *scene, const rf_camera *cams, int32_t n
                                float *g_sh, float *g_pos, void *stream);
 
 /*
+ * Extended forward / backward with the quantile loss of Eq. (6) (Sec. 3.3):
+ *   L_q = E_{u1,u2 ~ U[0,1]} |W^-1(u1) - W^-1(u2)|,
+ * W^-1 the quantile function of the ray's weight distribution T(t) sigma(t)
+ * normalised over the composited interval, i.e. 2 int F(1 - F) dt with
+ * F = (1 - T(t)) / (1 - T_final); 0 for a ray with no weight.  It is
+ * accumulated in the same walk as the colour (closed form per segment).
+ *
+ *   outputs of rf_render_fwd_ex (device, rays of all cameras concatenated):
+ *     rgb, trans, depth  required, as rf_render_fwd
+ *     steps, ray_status  optional
+ *     quantile           optional float [R]
+ *     quantile_aux       float [R][5], required with quantile: per-ray sums the
+ *                        backward of the quantile loss reads
+ */
+typedef struct rf_fwd_outputs {
+    float *rgb;
+    float *trans;
+    float *depth;
+    int32_t *steps;
+    uint8_t *ray_status;
+    float *quantile;
+    float *quantile_aux;
+} rf_fwd_outputs;
+
+/*   inputs of rf_render_bwd_ex (device):
+ *     rgb, trans, depth      forward outputs (depth may be NULL without d_depth)
+ *     quantile_aux           forward output, required with d_quantile
+ *     d_rgb                  required; d_trans, d_depth, d_quantile optional
+ *   gradients (device, FP32, accumulated +=, each may be NULL):
+ *     density [N], sh [N][(deg+1)^2][3], pos [N][3] */
+typedef struct rf_bwd_inputs {
+    const float *rgb;
+    const float *trans;
+    const float *depth;
+    const float *quantile_aux;
+    const float *d_rgb;
+    const float *d_trans;
+    const float *d_depth;
+    const float *d_quantile;
+} rf_bwd_inputs;
+
+typedef struct rf_grads {
+    float *density;
+    float *sh;
+    float *pos;
+} rf_grads;
+
+RF_API rf_status rf_render_fwd_ex(rf_scene *scene, const rf_camera *cams, int32_t n_cams,
+                                  const rf_render_opts *opts, const rf_fwd_outputs *out,
+                                  void *stream);
+RF_API rf_status rf_render_bwd_ex(rf_scene *scene, const rf_camera *cams, int32_t n_cams,
+                                  const rf_render_opts *opts, const rf_bwd_inputs *in,
+                                  const rf_grads *grads, void *stream);
+
+/*
  * Debug / parity: the cells each ray of one camera visits, in order.
  *   cells   device int32 [R][max_per_ray]  (-1 after the last cell)
  *   counts  device int32 [R]                total cells visited (may exceed

@@ -340,4 +340,54 @@ __device__ __forceinline__ void cell_step(const SceneDev &s, int i, const CellHd
     sh_colour<AT, DEG>(reinterpret_cast<const AT *>(s.sh), i, Y, g.pre, s.sh_v8 != 0);
 }
 
+// ---------------------------------------------------------------------------
+// Quantile loss (Eq. 6) pieces.  For a segment of width delta and density
+// sigma entered with transmittance T_n and accumulated weight W_n = 1 - T_n,
+// with x = sigma delta, g(x) = (1 - e^-x)/x and u(s) = 1 - e^{-sigma s}:
+//   A = int T/T_n = delta g,   C = int u (1 - u) = delta x g^2 / 2,
+//   int u = delta f1,  f1 = 1 - g,   int u^2 = delta f2,  f2 = f1 - x g^2 / 2.
+// With W(t) = 1 - T(t) = W_n + T_n u:
+//   Q = int W dt  (sum of W_n delta + T_n delta f1),
+//   Q2 = int W^2 dt (sum of W_n^2 delta + 2 W_n T_n delta f1 + T_n^2 delta f2),
+// and the loss is 2 int W (W_tot - W) dt / W_tot^2 = 2 (W_tot Q - Q2) / W_tot^2:
+// both terms are of the same order, so nearly transparent rays (small W_tot)
+// do not cancel.  f1, f2 use their series for small x.
+// ---------------------------------------------------------------------------
+struct QuantSeg {
+    float A, C, f1d, f2d;   // A, C, delta f1, delta f2
+    float dA_ds, dC_ds;     // d/dsigma at fixed delta
+    float alpha;            // 1 - e^-x, accurate for small x
+};
+
+__device__ __forceinline__ QuantSeg quant_seg(float sigma, float delta, float e) {
+    QuantSeg q;
+    const float x = sigma * delta;
+    if (x < 0.1f) {
+        // series in x, truncation error < 2e-8 relative at x = 0.1
+        const float f1 = x * (0.5f - x * (1.f / 6.f - x * (1.f / 24.f - x * (1.f / 120.f - x * (1.f / 720.f)))));
+        const float g = 1.f - f1;
+        const float f2 = x * x * (1.f / 3.f - x * (0.25f - x * (7.f / 60.f - x * (1.f / 24.f - x * (31.f / 2520.f)))));
+        q.A = delta * g;
+        q.f1d = delta * f1;
+        q.f2d = delta * f2;
+        q.alpha = x * g;
+        q.C = 0.5f * delta * x * g * g;
+        q.dA_ds = -delta * delta * (0.5f - x * (1.f / 3.f - x * (0.125f - x * (1.f / 30.f))));
+        q.dC_ds = 0.5f * delta * delta * (1.f - x * (2.f - x * (1.75f - x)));
+    } else {
+        const float alpha = -expm1f(-x);
+        const float g = alpha / x;
+        const float f1 = 1.f - g;
+        q.alpha = alpha;
+        q.A = delta * g;
+        q.f1d = delta * f1;
+        q.f2d = delta * (f1 - 0.5f * x * g * g);
+        q.C = 0.5f * delta * x * g * g;
+        const float s2 = sigma * sigma;
+        q.dA_ds = (x * e - alpha) / s2;
+        q.dC_ds = alpha * (2.f * x * e - alpha) / (2.f * s2);
+    }
+    return q;
+}
+
 }  // namespace rf

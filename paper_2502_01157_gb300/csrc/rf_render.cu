@@ -19,11 +19,18 @@ struct FwdOut {
     uint8_t *status;
     int32_t *trace;     // [R][max_trace] or null
     int32_t max_trace;
+    float *quantile;    // [R] (mode kQuant)
+    float *qaux;        // [R][5]: D, Q, W, Z1, Z2 (mode kQuant)
 };
 
-// Forward: Alg. 1 per ray with Eq. (3)-(4) compositing.
-template <typename AT, int DEG, bool TRACE>
+enum { kPlain = 0, kTrace = 1, kQuant = 2 };
+
+// Forward: Alg. 1 per ray with Eq. (3)-(4) compositing; in mode kQuant the
+// same walk also accumulates the quantile loss of Eq. (6).
+template <typename AT, int DEG, int MODE>
 __global__ void __launch_bounds__(kBlock) fwd_kernel(const RenderParams p, const FwdOut out) {
+    constexpr bool TRACE = MODE == kTrace;
+    constexpr bool QUANT = MODE == kQuant;
     const PixelTask px = pixel_of_thread(p.lc);
     if (!px.valid) return;
     const rf_camera &cam = p.lc.cam[px.cam];
@@ -32,6 +39,7 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const RenderParams p, const
     const int64_t r = p.lc.ray_begin[px.cam] + (int64_t)px.v * cam.width + px.u;
 
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, T = 1.f;
+    float qP = 0.f, qQ = 0.f, qW = 0.f, qZ1 = 0.f, qZ2 = 0.f;  // quantile-loss sums
     int steps = 0;
     uint8_t st = RF_RAY_OK;
     float tmin, tmax;
@@ -56,12 +64,30 @@ __global__ void __launch_bounds__(kBlock) fwd_kernel(const RenderParams p, const
             C1 = __fmaf_rn(w, fmaxf(g.pre[1], 0.f), C1);
             C2 = __fmaf_rn(w, fmaxf(g.pre[2], 0.f), C2);
             D = __fmaf_rn(w, __fmul_rn(0.5f, __fadd_rn(g.a, g.b)), D);
+            if (QUANT && g.delta > 0.f) {
+                const QuantSeg q = quant_seg(g.sigma, g.delta, g.e);
+                qQ += qW * g.delta + T * q.f1d;                            // int W
+                qP += qW * (qW * g.delta + 2.f * T * q.f1d) + T * T * q.f2d;  // int W^2
+                qZ1 += T * ((1.f - 2.f * T) * q.A + 2.f * T * q.C);
+                qZ2 += T * q.A;
+                qW += T * q.alpha;                                         // weight so far
+            }
             T = __fmul_rn(T, g.e);
             ++steps;
             if (g.next < 0 || !(g.t1 < tmax)) break;
             t0 = g.t1 > t0 ? g.t1 : t0;
             i = g.next;
         }
+    }
+    if (QUANT) {
+        const float qD = qW * qQ - qP;  // int W (W_tot - W) dt = int (1 - T)(T - T_f) dt
+        out.quantile[r] = qW > 0.f ? 2.f * qD / (qW * qW) : 0.f;
+        float *a = out.qaux + 5 * r;
+        a[0] = qD;
+        a[1] = qQ;
+        a[2] = qW;
+        a[3] = qZ1;
+        a[4] = qZ2;
     }
     if (TRACE) {
         for (int k = steps; k < out.max_trace; ++k) out.trace[r * out.max_trace + k] = -1;
@@ -82,6 +108,7 @@ struct BwdIO {
     const float *d_rgb, *d_trans, *d_depth;
     float *g_density, *g_sh, *g_pos;
     int32_t sh_vec;  // g_sh rows may use 16-byte atomics
+    const float *qaux, *d_quantile;
 };
 
 template <int DEG>
@@ -123,7 +150,7 @@ __device__ __forceinline__ void scatter_sh(float *__restrict__ g_sh, int i, cons
 // value.  A warp whose lanes are spread over many cells scatters per lane.
 constexpr int kMaxGroups = 12;
 
-template <typename AT, int DEG>
+template <typename AT, int DEG, bool QUANT>
 __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, const BwdIO io) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int NV = 3 * K;       // SH gradient row
@@ -155,12 +182,31 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
         gT = io.d_trans ? io.d_trans[r] : 0.f;
         gD = io.d_depth ? io.d_depth[r] : 0.f;
         live = !(gC[0] == 0.f && gC[1] == 0.f && gC[2] == 0.f && gT == 0.f && gD == 0.f);
+        if (QUANT) live = live || io.d_quantile[r] != 0.f;
         Cf[0] = io.rgb[3 * r];
         Cf[1] = io.rgb[3 * r + 1];
         Cf[2] = io.rgb[3 * r + 2];
         Tf = io.trans[r];
         Df = io.depth ? io.depth[r] : 0.f;
     }
+    // quantile loss L = 2 (P - T_f Q) / W^2: per-segment adjoints from the
+    // forward's sums; suffix sums of Z1 + T_f Z2 carry the dependence of the
+    // later segments on this segment's transmittance factor
+    float gQ = 0.f, qk2 = 0.f, qdTf = 0.f, qZ1 = 0.f, qZ2 = 0.f, qW = 0.f;
+    if (QUANT && live) {
+        gQ = io.d_quantile[r];
+        const float *a = io.qaux + 5 * r;
+        qW = a[2];
+        if (gQ != 0.f && qW > 0.f) {
+            qk2 = 2.f / (qW * qW);
+            qdTf = -qk2 * a[1] + 2.f * qk2 * a[0] / qW;  // dL/dT_f at fixed P, Q (a[0] = P - T_f Q)
+            qZ1 = a[3];
+            qZ2 = a[4];
+        } else {
+            gQ = 0.f;
+        }
+    }
+    float qWn = 0.f;  // weight before the current segment
     float Y[16];
     sh_basis<DEG>(d, Y);
     int i = live ? (int)(p.start_keys[p.lc.cam0 + px.cam] & 0xffffffffull) : 0;
@@ -217,7 +263,24 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
             // B = g_C.(T_{n+1} c_n - C_rest) - g_T T_final + g_D (T_{n+1} z_n - D_rest)
             const float B = gC[0] * (Tn * c[0] - (Cf[0] - C0)) + gC[1] * (Tn * c[1] - (Cf[1] - C1)) +
                             gC[2] * (Tn * c[2] - (Cf[2] - C2)) - gT * Tf + gD * (Tn * z - (Df - D));
-            sig_bar = io.g_density ? g.delta * B : 0.f;
+            float qsig = 0.f, qdel = 0.f;
+            if (QUANT && gQ != 0.f) {
+                float dP_ds = 0.f, dP_dd = 0.f, dQ_ds = 0.f, dQ_dd = 0.f;
+                if (g.delta > 0.f) {
+                    const QuantSeg q = quant_seg(g.sigma, g.delta, g.e);
+                    qZ1 -= T * ((1.f - 2.f * T) * q.A + 2.f * T * q.C);  // now the suffix over later segments
+                    qZ2 -= T * q.A;
+                    dP_ds = T * (qWn * q.dA_ds + T * q.dC_ds);
+                    dP_dd = T * g.e * (qWn + T * q.alpha);
+                    dQ_ds = -T * q.dA_ds;
+                    dQ_dd = qWn + T * q.alpha;
+                    qWn += T * q.alpha;
+                }
+                const float later = qk2 * (qZ1 + Tf * qZ2) + qdTf * Tf;
+                qsig = gQ * (qk2 * (dP_ds - Tf * dQ_ds) - g.delta * later);
+                qdel = gQ * (qk2 * (dP_dd - Tf * dQ_dd) - g.sigma * later);
+            }
+            sig_bar = io.g_density ? g.delta * B + qsig : 0.f;
             if (io.g_sh) {
                 cb[0] = g.pre[0] > 0.f ? gC[0] * w : 0.f;
                 cb[1] = g.pre[1] > 0.f ? gC[1] * w : 0.f;
@@ -225,7 +288,7 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
             }
             // segment bounds: delta = max(b - a, 0), z = (a + b)/2,
             // a = max(t0, t_min), b = min(t1, t_max)
-            const float dbar = g.sigma * B;
+            const float dbar = g.sigma * B + qdel;
             float abar = 0.5f * gD * w, bbar = abar;
             if (g.b > g.a) {
                 bbar += dbar;
@@ -373,14 +436,16 @@ __global__ void mse_grad_kernel(const float *__restrict__ rgb, const float *__re
 // Host side
 // ---------------------------------------------------------------------------
 template <typename AT, int DEG>
-static void launch_fwd(bool trace, int64_t tiles, const RenderParams &p, const FwdOut &o, cudaStream_t st) {
-    if (trace) fwd_kernel<AT, DEG, true><<<(unsigned)tiles, kBlock, 0, st>>>(p, o);
-    else fwd_kernel<AT, DEG, false><<<(unsigned)tiles, kBlock, 0, st>>>(p, o);
+static void launch_fwd(int mode, int64_t tiles, const RenderParams &p, const FwdOut &o, cudaStream_t st) {
+    if (mode == kTrace) fwd_kernel<AT, DEG, kTrace><<<(unsigned)tiles, kBlock, 0, st>>>(p, o);
+    else if (mode == kQuant) fwd_kernel<AT, DEG, kQuant><<<(unsigned)tiles, kBlock, 0, st>>>(p, o);
+    else fwd_kernel<AT, DEG, kPlain><<<(unsigned)tiles, kBlock, 0, st>>>(p, o);
 }
 
 template <typename AT, int DEG>
-static void launch_bwd(int64_t tiles, const RenderParams &p, const BwdIO &io, cudaStream_t st) {
-    bwd_kernel<AT, DEG><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
+static void launch_bwd(bool quant, int64_t tiles, const RenderParams &p, const BwdIO &io, cudaStream_t st) {
+    if (quant) bwd_kernel<AT, DEG, true><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
+    else bwd_kernel<AT, DEG, false><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
 }
 
 template <typename F>
@@ -429,9 +494,9 @@ rf_status launch_fwd_batch(const rf_scene *s, const rf_camera *cams, const int64
     if (rc != RF_OK) return rc;
     const int64_t tiles = make_launch_cams(cams, 0, n, 0, &p.lc);
     for (int c = 0; c < n; ++c) p.lc.ray_begin[c] = ray_offsets[c];
-    FwdOut out = {rgb, trans, depth, nullptr, nullptr, nullptr, 0};
+    FwdOut out = {rgb, trans, depth, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     dispatch(s->attr_dtype, s->sh_degree, [&]<typename AT, int DEG>() {
-        launch_fwd<AT, DEG>(false, tiles, p, out, st);
+        launch_fwd<AT, DEG>(kPlain, tiles, p, out, st);
     });
     RF_CUDA(cudaGetLastError());
     return RF_OK;
@@ -442,7 +507,7 @@ rf_status launch_fwd_batch(const rf_scene *s, const rf_camera *cams, const int64
 using namespace rf;
 
 static rf_status render_fwd_impl(rf_scene *s, const rf_camera *cams, int32_t n_cams,
-                                 const rf_render_opts *opts, FwdOut out, bool trace, void *stream) {
+                                 const rf_render_opts *opts, FwdOut out, int mode, void *stream) {
     float eps;
     int32_t max_steps;
     rf_status rc = common_checks(s, cams, n_cams, opts, &eps, &max_steps);
@@ -463,27 +528,77 @@ static rf_status render_fwd_impl(rf_scene *s, const rf_camera *cams, int32_t n_c
         if (tiles >= (1ll << 31)) return fail(RF_ERR_INVALID_ARG, "too many tiles in one launch");
         for (int c = 0; c < count; ++c) ray_begin += (int64_t)cams[first + c].width * cams[first + c].height;
         dispatch(s->attr_dtype, s->sh_degree, [&]<typename AT, int DEG>() {
-            launch_fwd<AT, DEG>(trace, tiles, p, out, st);
+            launch_fwd<AT, DEG>(mode, tiles, p, out, st);
         });
         RF_CUDA(cudaGetLastError());
     }
     return RF_OK;
 }
 
+RF_API rf_status rf_render_fwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_cams,
+                                  const rf_render_opts *opts, const rf_fwd_outputs *o, void *stream) {
+    if (!o || !o->rgb || !o->trans || !o->depth)
+        return fail(RF_ERR_INVALID_ARG, "rgb, trans and depth are required");
+    if (o->quantile && !o->quantile_aux)
+        return fail(RF_ERR_INVALID_ARG, "quantile_aux is required with quantile");
+    FwdOut out = {o->rgb, o->trans, o->depth, o->steps, o->ray_status, nullptr, 0, o->quantile,
+                  o->quantile_aux};
+    return render_fwd_impl(s, cams, n_cams, opts, out, o->quantile ? kQuant : kPlain, stream);
+}
+
 RF_API rf_status rf_render_fwd(rf_scene *s, const rf_camera *cams, int32_t n_cams,
                                const rf_render_opts *opts, float *rgb, float *trans, float *depth,
                                int32_t *steps, uint8_t *ray_status, void *stream) {
-    if (!rgb || !trans || !depth) return fail(RF_ERR_INVALID_ARG, "rgb, trans and depth are required");
-    FwdOut out = {rgb, trans, depth, steps, ray_status, nullptr, 0};
-    return render_fwd_impl(s, cams, n_cams, opts, out, false, stream);
+    const rf_fwd_outputs o = {rgb, trans, depth, steps, ray_status, nullptr, nullptr};
+    return rf_render_fwd_ex(s, cams, n_cams, opts, &o, stream);
 }
 
 RF_API rf_status rf_trace_cells(rf_scene *s, const rf_camera *cam, const rf_render_opts *opts,
                                 int32_t max_per_ray, int32_t *cells, int32_t *counts, void *stream) {
     if (!cells || !counts || max_per_ray < 1)
         return fail(RF_ERR_INVALID_ARG, "cells, counts and max_per_ray >= 1 are required");
-    FwdOut out = {nullptr, nullptr, nullptr, counts, nullptr, cells, max_per_ray};
-    return render_fwd_impl(s, cam, 1, opts, out, true, stream);
+    FwdOut out = {nullptr, nullptr, nullptr, counts, nullptr, cells, max_per_ray, nullptr, nullptr};
+    return render_fwd_impl(s, cam, 1, opts, out, kTrace, stream);
+}
+
+RF_API rf_status rf_render_bwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_cams,
+                                  const rf_render_opts *opts, const rf_bwd_inputs *in,
+                                  const rf_grads *gr, void *stream) {
+    float eps;
+    int32_t max_steps;
+    rf_status rc = common_checks(s, cams, n_cams, opts, &eps, &max_steps);
+    if (rc != RF_OK) return rc;
+    if (!in || !gr) return fail(RF_ERR_INVALID_ARG, "inputs and gradients must not be NULL");
+    if (!in->rgb || !in->trans || !in->d_rgb) return fail(RF_ERR_INVALID_ARG, "rgb, trans and d_rgb are required");
+    if (in->d_depth && !in->depth) return fail(RF_ERR_INVALID_ARG, "depth is required with d_depth");
+    if (in->d_quantile && !in->quantile_aux)
+        return fail(RF_ERR_INVALID_ARG, "quantile_aux is required with d_quantile");
+    if (!gr->density && !gr->sh && !gr->pos) return RF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    BwdIO io = {in->rgb, in->trans, in->depth, in->d_rgb, in->d_trans, in->d_depth, gr->density,
+                gr->sh, gr->pos, (int32_t)(((uintptr_t)gr->sh & 15) == 0), in->quantile_aux,
+                in->d_quantile};
+    const bool quant = in->d_quantile != nullptr;
+    RenderParams p;
+    memset(&p, 0, sizeof p);
+    p.s = scene_dev(s);
+    p.start_keys = s->start_keys;
+    p.eps = eps;
+    p.max_steps = max_steps;
+    int64_t ray_begin = 0;
+    for (int first = 0; first < n_cams; first += kMaxCamsPerLaunch) {
+        const int count = n_cams - first < kMaxCamsPerLaunch ? n_cams - first : kMaxCamsPerLaunch;
+        rc = launch_nearest_sites(s, cams + first, count, s->start_keys, st);
+        if (rc != RF_OK) return rc;
+        const int64_t tiles = make_launch_cams(cams, first, count, ray_begin, &p.lc);
+        if (tiles >= (1ll << 31)) return fail(RF_ERR_INVALID_ARG, "too many tiles in one launch");
+        for (int c = 0; c < count; ++c) ray_begin += (int64_t)cams[first + c].width * cams[first + c].height;
+        dispatch(s->attr_dtype, s->sh_degree, [&]<typename AT, int DEG>() {
+            launch_bwd<AT, DEG>(quant, tiles, p, io, st);
+        });
+        RF_CUDA(cudaGetLastError());
+    }
+    return RF_OK;
 }
 
 RF_API rf_status rf_render_bwd(rf_scene *s, const rf_camera *cams, int32_t n_cams,
@@ -491,36 +606,9 @@ RF_API rf_status rf_render_bwd(rf_scene *s, const rf_camera *cams, int32_t n_cam
                                const float *depth, const float *d_rgb, const float *d_trans,
                                const float *d_depth, float *g_density, float *g_sh, float *g_pos,
                                void *stream) {
-    float eps;
-    int32_t max_steps;
-    rf_status rc = common_checks(s, cams, n_cams, opts, &eps, &max_steps);
-    if (rc != RF_OK) return rc;
-    if (!rgb || !trans || !d_rgb) return fail(RF_ERR_INVALID_ARG, "rgb, trans and d_rgb are required");
-    if (d_depth && !depth) return fail(RF_ERR_INVALID_ARG, "depth is required with d_depth");
-    if (!g_density && !g_sh && !g_pos) return RF_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    BwdIO io = {rgb, trans, depth, d_rgb, d_trans, d_depth, g_density, g_sh, g_pos,
-                (int32_t)(((uintptr_t)g_sh & 15) == 0)};
-    RenderParams p;
-    memset(&p, 0, sizeof p);
-    p.s = scene_dev(s);
-    p.start_keys = s->start_keys;
-    p.eps = eps;
-    p.max_steps = max_steps;
-    int64_t ray_begin = 0;
-    for (int first = 0; first < n_cams; first += kMaxCamsPerLaunch) {
-        const int count = n_cams - first < kMaxCamsPerLaunch ? n_cams - first : kMaxCamsPerLaunch;
-        rc = launch_nearest_sites(s, cams + first, count, s->start_keys, st);
-        if (rc != RF_OK) return rc;
-        const int64_t tiles = make_launch_cams(cams, first, count, ray_begin, &p.lc);
-        if (tiles >= (1ll << 31)) return fail(RF_ERR_INVALID_ARG, "too many tiles in one launch");
-        for (int c = 0; c < count; ++c) ray_begin += (int64_t)cams[first + c].width * cams[first + c].height;
-        dispatch(s->attr_dtype, s->sh_degree, [&]<typename AT, int DEG>() {
-            launch_bwd<AT, DEG>(tiles, p, io, st);
-        });
-        RF_CUDA(cudaGetLastError());
-    }
-    return RF_OK;
+    const rf_bwd_inputs in = {rgb, trans, depth, nullptr, d_rgb, d_trans, d_depth, nullptr};
+    const rf_grads gr = {g_density, g_sh, g_pos};
+    return rf_render_bwd_ex(s, cams, n_cams, opts, &in, &gr, stream);
 }
 
 RF_API rf_status rf_mse_grad(const float *rgb, const float *target, int64_t n, float scale,

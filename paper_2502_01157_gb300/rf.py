@@ -67,6 +67,23 @@ class rf_serve_metrics(ctypes.Structure):
                 ("max_busy_streams", ctypes.c_int32), ("inflight", ctypes.c_int32)]
 
 
+class rf_fwd_outputs(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("trans", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("steps", ctypes.c_void_p), ("ray_status", ctypes.c_void_p),
+                ("quantile", ctypes.c_void_p), ("quantile_aux", ctypes.c_void_p)]
+
+
+class rf_bwd_inputs(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("trans", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("quantile_aux", ctypes.c_void_p), ("d_rgb", ctypes.c_void_p),
+                ("d_trans", ctypes.c_void_p), ("d_depth", ctypes.c_void_p),
+                ("d_quantile", ctypes.c_void_p)]
+
+
+class rf_grads(ctypes.Structure):
+    _fields_ = [("density", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("pos", ctypes.c_void_p)]
+
+
 class RFError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"rf error {code}: {msg}")
@@ -93,6 +110,11 @@ SIGNATURES = {
     "rf_render_bwd": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.c_int32,
                            ctypes.POINTER(rf_render_opts), _P, _P, _P, _P, _P, _P, _P, _P, _P,
                            _P]),
+    "rf_render_fwd_ex": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.c_int32,
+                              ctypes.POINTER(rf_render_opts), ctypes.POINTER(rf_fwd_outputs), _P]),
+    "rf_render_bwd_ex": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.c_int32,
+                              ctypes.POINTER(rf_render_opts), ctypes.POINTER(rf_bwd_inputs),
+                              ctypes.POINTER(rf_grads), _P]),
     "rf_trace_cells": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.POINTER(rf_render_opts),
                             ctypes.c_int32, _P, _P, _P]),
     "rf_mse_grad": (_S, [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
@@ -148,6 +170,11 @@ def _ptr(t: Optional[torch.Tensor]):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _addr(t: Optional[torch.Tensor]):
+    p = _ptr(t)
+    return None if p is None else p.value
 
 
 def _stream(stream=None) -> ctypes.c_void_p:
@@ -274,9 +301,10 @@ class Foam:
             self.update_positions(pos.detach())
 
     def render(self, cams, eps: float = 1e-4, max_steps: int = 0, steps: bool = False,
-               status: bool = False, out=None, stream=None) -> dict:
+               status: bool = False, quantile: bool = False, out=None, stream=None) -> dict:
         """Forward render; returns rgb [R,3], trans [R], depth [R] (+ steps,
-        status) as CUDA tensors, rays of the cameras concatenated."""
+        status; + quantile [R] and quantile_aux [R,5] with ``quantile``) as
+        CUDA tensors, rays of the cameras concatenated."""
         ca = camera_array(cams)
         R = n_rays_of(cams)
         dev = self.pos.device
@@ -287,17 +315,22 @@ class Foam:
                 out["steps"] = torch.empty(R, dtype=torch.int32, device=dev)
             if status:
                 out["status"] = torch.empty(R, dtype=torch.uint8, device=dev)
+            if quantile:
+                out["quantile"] = torch.empty(R, device=dev)
+                out["quantile_aux"] = torch.empty(R, 5, device=dev)
         o = opts_struct(eps, max_steps)
-        _check(lib().rf_render_fwd(self.handle, ca, len(ca), ctypes.byref(o), _ptr(out["rgb"]),
-                                   _ptr(out["trans"]), _ptr(out["depth"]),
-                                   _ptr(out.get("steps")), _ptr(out.get("status")),
-                                   _stream(stream)))
+        fo = rf_fwd_outputs(_addr(out["rgb"]), _addr(out["trans"]), _addr(out["depth"]),
+                            _addr(out.get("steps")), _addr(out.get("status")),
+                            _addr(out.get("quantile")), _addr(out.get("quantile_aux")))
+        _check(lib().rf_render_fwd_ex(self.handle, ca, len(ca), ctypes.byref(o), ctypes.byref(fo),
+                                      _stream(stream)))
         return out
 
     def backward(self, cams, fwd: dict, d_rgb, d_trans=None, d_depth=None, grads=None,
-                 eps: float = 1e-4, max_steps: int = 0, stream=None) -> dict:
+                 eps: float = 1e-4, max_steps: int = 0, d_quantile=None, stream=None) -> dict:
         """Accumulate gradients (density, sh, pos; float32) of the forward
-        outputs into ``grads`` (zero-initialised if None)."""
+        outputs (and of the quantile loss, with ``d_quantile``) into ``grads``
+        (zero-initialised if None)."""
         if grads is None:
             dev = self.pos.device
             grads = dict(density=torch.zeros(self.n_sites, device=dev),
@@ -305,11 +338,12 @@ class Foam:
                          pos=torch.zeros(self.n_sites, 3, device=dev))
         ca = camera_array(cams)
         o = opts_struct(eps, max_steps)
-        _check(lib().rf_render_bwd(self.handle, ca, len(ca), ctypes.byref(o), _ptr(fwd["rgb"]),
-                                   _ptr(fwd["trans"]), _ptr(fwd.get("depth")), _ptr(d_rgb),
-                                   _ptr(d_trans), _ptr(d_depth), _ptr(grads.get("density")),
-                                   _ptr(grads.get("sh")), _ptr(grads.get("pos")),
-                                   _stream(stream)))
+        bi = rf_bwd_inputs(_addr(fwd["rgb"]), _addr(fwd["trans"]), _addr(fwd.get("depth")),
+                           _addr(fwd.get("quantile_aux")), _addr(d_rgb), _addr(d_trans),
+                           _addr(d_depth), _addr(d_quantile))
+        go = rf_grads(_addr(grads.get("density")), _addr(grads.get("sh")), _addr(grads.get("pos")))
+        _check(lib().rf_render_bwd_ex(self.handle, ca, len(ca), ctypes.byref(o), ctypes.byref(bi),
+                                      ctypes.byref(go), _stream(stream)))
         return grads
 
     def trace(self, cam, max_per_ray: int = 256, eps: float = 1e-4, max_steps: int = 0,
@@ -373,50 +407,58 @@ def render_noalloc(pos, adj_off, adj_idx, density, sh, aabb, cams, eps: float = 
 
 class _Render(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, foam, cams, eps, max_steps, density, sh, pos):
+    def forward(ctx, foam, cams, eps, max_steps, quantile, density, sh, pos):
         foam._sync_positions(pos)
-        out = foam.render(cams, eps=eps, max_steps=max_steps)
-        ctx.foam, ctx.cams, ctx.eps, ctx.max_steps = foam, cams, eps, max_steps
+        out = foam.render(cams, eps=eps, max_steps=max_steps, quantile=quantile)
+        ctx.foam, ctx.cams, ctx.eps, ctx.max_steps, ctx.quantile = foam, cams, eps, max_steps, quantile
         ctx.dtypes = (density.dtype, sh.dtype)
+        if quantile:
+            ctx.save_for_backward(out["rgb"], out["trans"], out["depth"], out["quantile_aux"])
+            return out["rgb"], out["trans"], out["depth"], out["quantile"]
         ctx.save_for_backward(out["rgb"], out["trans"], out["depth"])
         return out["rgb"], out["trans"], out["depth"]
 
     @staticmethod
-    def backward(ctx, g_rgb, g_trans, g_depth):
-        rgb, trans, depth = ctx.saved_tensors
+    def backward(ctx, g_rgb, g_trans, g_depth, g_quant=None):
+        saved = ctx.saved_tensors
+        rgb, trans, depth = saved[:3]
         foam = ctx.foam
         need = ctx.needs_input_grad
         dev = rgb.device
         grads = {}
-        if need[4]:
-            grads["density"] = torch.zeros(foam.n_sites, device=dev)
         if need[5]:
-            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+            grads["density"] = torch.zeros(foam.n_sites, device=dev)
         if need[6]:
+            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+        if need[7]:
             grads["pos"] = torch.zeros(foam.n_sites, 3, device=dev)
         if grads:
             z = lambda g: None if g is None else g.contiguous().float()
-            foam.backward(ctx.cams, dict(rgb=rgb, trans=trans, depth=depth),
+            fwd = dict(rgb=rgb, trans=trans, depth=depth)
+            if ctx.quantile:
+                fwd["quantile_aux"] = saved[3]
+            foam.backward(ctx.cams, fwd,
                           z(g_rgb) if g_rgb is not None else torch.zeros_like(rgb),
                           z(g_trans), z(g_depth), grads=grads, eps=ctx.eps,
-                          max_steps=ctx.max_steps)
+                          max_steps=ctx.max_steps, d_quantile=z(g_quant) if ctx.quantile else None)
         gd = grads.get("density")
         gs = grads.get("sh")
-        return (None, None, None, None,
+        return (None, None, None, None, None,
                 None if gd is None else gd.to(ctx.dtypes[0]),
                 None if gs is None else gs.to(ctx.dtypes[1]),
                 grads.get("pos"))
 
 
 def render(foam: Foam, cams, density=None, sh=None, pos=None, eps: float = 1e-4,
-           max_steps: int = 0):
+           max_steps: int = 0, quantile: bool = False):
     """Differentiable render of ``cams``: returns (rgb [R,3], trans [R],
-    depth [R]); gradients flow to ``density``, ``sh`` and ``pos`` (defaults:
-    the foam's own tensors).  A changed ``pos`` is re-packed first."""
+    depth [R]) and, with ``quantile``, the per-ray quantile loss of Eq. (6)
+    [R]; gradients flow to ``density``, ``sh`` and ``pos`` (defaults: the
+    foam's own tensors).  A changed ``pos`` is re-packed first."""
     density = foam.density if density is None else density
     sh = foam.sh if sh is None else sh
     if density is not foam.density or sh is not foam.sh:
         foam.set_attributes(density.detach(), sh.detach())
     if pos is None:
         pos = foam.pos
-    return _Render.apply(foam, cams, eps, max_steps, density, sh, pos)
+    return _Render.apply(foam, cams, eps, max_steps, bool(quantile), density, sh, pos)

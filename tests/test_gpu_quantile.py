@@ -1,0 +1,125 @@
+"""Quantile loss of Eq. (6) fused into the walk: CUDA path against the FP64
+oracle (values per ray and gradients), and the fused forward leaves the
+colour / transmittance / depth outputs bit-identical."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2502_01157_gb300 import rf
+from paper_2502_01157_gb300 import scenes as S
+from tests.helpers import camera_at, random_scene
+from tests.parity import GRAD_REL, foam_of, rel_l2, rounded_scene
+
+pytestmark = pytest.mark.gpu
+Q_RMSE = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+
+
+def _cams():
+    return [camera_at((0.05, 0.1, -0.02), (0.2, -0.3, 1.0), w=37, h=21),
+            camera_at((2.5, -1.0, 1.2), (0.0, 0.0, 0.0), w=19, h=17)]
+
+
+@pytest.mark.parametrize("deg,dt,scale", [(0, "f32", 1.0), (3, "f32", 1.0), (3, "bf16", 1.0),
+                                          (1, "f32", 40.0), (2, "f32", 0.002)])
+def test_quantile_forward_and_backward_match_oracle(deg, dt, scale):
+    sc = random_scene(2500, deg, 400 + deg)
+    sc.density[:] *= scale   # 40: early stops inside the foam; 0.002: nearly transparent rays
+    cams = _cams()
+    foam = foam_of(sc, dt)
+    ref = rounded_scene(sc, dt)
+    plain = foam.render(cams)
+    out = foam.render(cams, quantile=True)
+    torch.cuda.synchronize()
+    for k in ("rgb", "trans", "depth"):
+        assert torch.equal(plain[k], out[k]), k
+    q = out["quantile"].cpu().numpy()
+    R = rf.n_rays_of(cams)
+    rng = np.random.default_rng(deg)
+    gq = rng.normal(size=R).astype(np.float32)
+    gr = rng.normal(size=(R, 3)).astype(np.float32)
+    base = 0
+    ref_g = dict(density=0, sh=0, pos=0)
+    for cam in cams:
+        sl = slice(base, base + cam.n_rays)
+        qo = oracle.render_quantile(ref, cam)
+        err = np.sqrt(np.mean((q[sl] - qo) ** 2))
+        rel = np.max(np.abs(q[sl] - qo) / np.maximum(qo, 1e-3))
+        print(f"deg {deg} {dt} x{scale}: quantile rmse {err:.2e}, max rel {rel:.2e}, mean {qo.mean():.3f}")
+        assert err <= Q_RMSE
+        o = oracle.render(ref, cam)
+        gq[sl][o["degen"]] = 0
+        gr[sl][o["degen"]] = 0
+        G = oracle.render_bwd(ref, cam, gr[sl], g_quantile=gq[sl])
+        for k in ref_g:
+            ref_g[k] = ref_g[k] + G[k]
+        base += cam.n_rays
+    t = lambda a: torch.from_numpy(a).cuda()
+    G = foam.backward(cams, out, t(gr), d_quantile=t(gq))
+    torch.cuda.synchronize()
+    for k in ref_g:
+        e = rel_l2(G[k].cpu().numpy(), ref_g[k])
+        print(f"  grad {k}: rel err {e:.2e}")
+        assert e <= GRAD_REL, k
+
+
+def test_quantile_alone_has_no_colour_gradient():
+    sc = random_scene(1500, 2, 11)
+    foam = foam_of(sc)
+    cams = _cams()
+    out = foam.render(cams, quantile=True)
+    R = rf.n_rays_of(cams)
+    G = foam.backward(cams, out, torch.zeros(R, 3, device="cuda"),
+                      d_quantile=torch.ones(R, device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(G["sh"]) == 0
+    assert torch.count_nonzero(G["density"]) > 0 and torch.count_nonzero(G["pos"]) > 0
+
+
+def test_quantile_autograd_matches_direct_backward():
+    sc = random_scene(1500, 1, 21)
+    foam = foam_of(sc)
+    cam = camera_at((0.1, 0.1, 0.1), (0.0, 1.0, 0.0), w=24, h=16)
+    dens = foam.density.clone().requires_grad_(True)
+    sh = foam.sh.clone().requires_grad_(True)
+    pos = foam.pos.clone().requires_grad_(True)
+    rgb, tr, dp, q = rf.render(foam, [cam], dens, sh, pos, quantile=True)
+    (rgb.sum() + 0.3 * q.sum()).backward()
+    fwd = foam.render([cam], quantile=True)
+    G = foam.backward([cam], fwd, torch.ones_like(fwd["rgb"]),
+                      d_quantile=torch.full_like(fwd["quantile"], 0.3))
+    torch.testing.assert_close(dens.grad, G["density"], rtol=1e-5, atol=1e-6)
+    torch.testing.assert_close(pos.grad, G["pos"], rtol=1e-5, atol=1e-6)
+
+
+def test_quantile_full_size_c3_sampled():
+    sc = S.config_scene("c3")
+    cam = S.config_cameras("c3")[0]
+    foam = foam_of(sc)
+    out = foam.render([cam], quantile=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    px = np.sort(rng.choice(cam.n_rays, size=600, replace=False))
+    q = out["quantile"].cpu().numpy()[px]
+    qo = oracle.render_quantile(sc, cam, pixels=px)
+    err = np.sqrt(np.mean((q - qo) ** 2))
+    print(f"c3 quantile rmse {err:.2e} (mean {qo.mean():.3f})")
+    assert err <= Q_RMSE
+    o = oracle.render(sc, cam, pixels=px)
+    keep = px[~o["degen"]]
+    gq = np.zeros(cam.n_rays, np.float32)
+    gq[keep] = rng.normal(size=len(keep)).astype(np.float32)
+    G = foam.backward([cam], out, torch.zeros(cam.n_rays, 3, device="cuda"),
+                      d_quantile=torch.from_numpy(gq).cuda())
+    torch.cuda.synchronize()
+    Go = oracle.render_bwd(sc, cam, np.zeros((len(keep), 3)), pixels=keep, g_quantile=gq[keep])
+    for k in ("density", "pos"):
+        e = rel_l2(G[k].cpu().numpy(), Go[k])
+        print(f"c3 quantile grad {k}: rel err {e:.2e}")
+        assert e <= GRAD_REL
