@@ -72,9 +72,10 @@ def rank_camera(workload, rank):
 
 
 def bytes_per_step(k_bar, deg, attr_bytes):
-    """Algorithmic bytes one cell step reads (no reuse): cell record 16 B,
-    next offset 4 B, K faces x 16 B, density and SH coefficients."""
-    return 16 + 4 + 16 * k_bar + attr_bytes + 3 * (deg + 1) ** 2 * attr_bytes
+    """Algorithmic bytes one cell step reads (no reuse): cell header 16 B,
+    K faces x 12 B, the exit face's neighbour id 4 B, density and SH
+    coefficients."""
+    return 16 + 12 * k_bar + 4 + attr_bytes + 3 * (deg + 1) ** 2 * attr_bytes
 
 
 def bwd_extra_bytes_per_step(deg):

@@ -13,10 +13,12 @@
 struct rf_scene {
     int64_t n_sites = 0;
     int64_t n_edges = 0;
-    float4 *cells = nullptr;     // [N]: {x, y, z, begin}
-    int32_t *off = nullptr;      // [N+1] offsets of the padded face lists (ends = off + 1)
-    float4 *faces = nullptr;     // [n_slots] face records (even-aligned, even-length lists)
-    int64_t n_slots = 0;
+    float4 *cells = nullptr;     // [N]: {x, y, z, first_group << count_bits | n_groups}
+    int32_t *off = nullptr;      // [N+1] first face group of each cell
+    float4 *faces = nullptr;     // [3 n_groups]: u_x, u_y, u_z of four faces per group
+    int32_t *nbr = nullptr;      // [4 n_groups]: neighbour ids (-1: padding)
+    int64_t n_groups = 0;
+    int32_t count_bits = 4;
     const void *density = nullptr;  // borrowed
     const void *sh = nullptr;       // borrowed
     int32_t sh_degree = 0;

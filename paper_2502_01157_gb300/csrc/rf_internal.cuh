@@ -26,26 +26,27 @@ constexpr int kDefaultMaxSteps = 1 << 16;
 
 // ---------------------------------------------------------------------------
 // Packed scene (device memory owned by rf_scene)
-//   cells[i] = {x_i, y_i, z_i, bits(begin)}, ends[i] = end of the face list
-//       (the forward is bound by the bytes the L1 delivers to the lanes, so
-//       the header is kept at 20 bytes)
-//   faces[f] = {u_x, u_y, u_z, bits(j)} for the directed edge (i, j),
-//       u = 2 (p_j - p_i) / |p_j - p_i|^2.  Each cell's list starts at an
-//       even index and has an even length (padded with {0, 0, 0, -1}, which
-//       is never front-facing), so faces are read two per 256-bit load.
+//   cells[i] = {x_i, y_i, z_i, bits(first_group << count_bits | n_groups)}
+//   faces: the neighbours of cell i in groups of four, three float4 per group
+//       {u_x of faces 0..3}, {u_y 0..3}, {u_z 0..3} (12 bytes per face),
+//       u = 2 (p_j - p_i) / |p_j - p_i|^2; nbr[4 g + k] = j (-1: padding, u = 0)
+// The forward is bound by the bytes the L1 delivers to the lanes per cell
+// step, so a step reads a 16-byte header, 12 bytes per face and one 4-byte
+// neighbour id (of the exit face only).
 // With o~ = o - p_i the bisector of (p_i, p_j) is crossed at
 //   t = (1 - u . o~) / (u . d),
 // front-facing (an exit, Fig. 3) iff u . d > 0.
 // ---------------------------------------------------------------------------
 struct SceneDev {
     const float4 *cells;
-    const int32_t *ends;
     const float4 *faces;
+    const int32_t *nbr;
     const void *density;
     const void *sh;
     float box_lo[3];
     float box_hi[3];
-    int32_t sh_v8;  // SH rows are 32-byte aligned (base and row size)
+    int32_t count_bits;  // low bits of a header's w that hold its group count
+    int32_t sh_v8;       // SH rows are 32-byte aligned (base and row size)
 };
 
 // Cameras of one launch and the tile partition of their images.
@@ -82,12 +83,13 @@ __device__ __forceinline__ void ldg256(const void *p, uint32_t (&v)[8]) {
 
 struct CellHdr {
     float x, y, z;
-    int begin, end;
+    int gbeg, gcnt;  // first face group, number of groups
 };
 
 __device__ __forceinline__ CellHdr load_cell(const SceneDev &s, int i) {
     const float4 h = __ldg(s.cells + i);
-    return {h.x, h.y, h.z, __float_as_int(h.w), __ldg(s.ends + i)};
+    const uint32_t w = __float_as_uint(h.w);
+    return {h.x, h.y, h.z, (int)(w >> s.count_bits), (int)(w & ((1u << s.count_bits) - 1u))};
 }
 
 __device__ __forceinline__ float to_f(float v) { return v; }
@@ -279,37 +281,35 @@ __device__ __forceinline__ void sh_colour(const AT *__restrict__ sh, int i, cons
 // Exit face of cell i (Alg. 1 inner loop): the front-facing bisector with the
 // smallest crossing parameter, first in adjacency order on ties.  The
 // comparison t_j < t_best is done by cross-multiplication (both denominators
-// are positive), so no division is needed per face.  Faces come in pairs
-// (one 256-bit load); padding records have u = 0 and are never exits.
-// Returns j or -1.
-__device__ __forceinline__ void face_test(uint32_t ux, uint32_t uy, uint32_t uz, uint32_t j,
-                                          const float3 &d, const float3 &oc, float &nb, float &db,
-                                          int &jb) {
-    const float x = __uint_as_float(ux), y = __uint_as_float(uy), z = __uint_as_float(uz);
+// are positive), so no division is needed per face.  Padding faces have
+// u = 0 and are never exits.  Returns j or -1.
+__device__ __forceinline__ void face_test(float x, float y, float z, int slot, const float3 &d,
+                                          const float3 &oc, float &nb, float &db, int &fb) {
     const float den = __fmaf_rn(x, d.x, __fmaf_rn(y, d.y, __fmul_rn(z, d.z)));
     const float num = __fmaf_rn(-x, oc.x, __fmaf_rn(-y, oc.y, __fmaf_rn(-z, oc.z, 1.f)));
     if (den > 0.f && __fmul_rn(num, db) < __fmul_rn(nb, den)) {
         nb = num;
         db = den;
-        jb = (int)j;
+        fb = slot;
     }
 }
 
-__device__ __forceinline__ int find_exit(const float4 *__restrict__ faces, int begin, int end,
-                                         const float3 &d, const float3 &oc, float &num_best,
-                                         float &den_best) {
+__device__ __forceinline__ int find_exit(const SceneDev &s, const CellHdr &c, const float3 &d,
+                                         const float3 &oc, float &num_best, float &den_best) {
     float nb = 1.f, db = 0.f;
-    int jb = -1;
+    int fb = -1;
+    const float4 *f = s.faces + 3 * (size_t)c.gbeg;
 #pragma unroll 2
-    for (int f = begin; f < end; f += 2) {
-        uint32_t v[8];
-        ldg256(faces + f, v);
-        face_test(v[0], v[1], v[2], v[3], d, oc, nb, db, jb);
-        face_test(v[4], v[5], v[6], v[7], d, oc, nb, db, jb);
+    for (int g = 0; g < c.gcnt; ++g) {
+        const float4 X = ldg(f + 3 * g), Y = ldg(f + 3 * g + 1), Z = ldg(f + 3 * g + 2);
+        face_test(X.x, Y.x, Z.x, 4 * g + 0, d, oc, nb, db, fb);
+        face_test(X.y, Y.y, Z.y, 4 * g + 1, d, oc, nb, db, fb);
+        face_test(X.z, Y.z, Z.z, 4 * g + 2, d, oc, nb, db, fb);
+        face_test(X.w, Y.w, Z.w, 4 * g + 3, d, oc, nb, db, fb);
     }
     num_best = nb;
     den_best = db;
-    return jb;
+    return fb >= 0 ? ldg(s.nbr + 4 * (size_t)c.gbeg + fb) : -1;
 }
 
 // One segment's bounds, width, density and colour (shared by all kernels).
@@ -329,7 +329,7 @@ __device__ __forceinline__ void cell_step(const SceneDev &s, int i, const CellHd
                                           float tmax, const float *Y, Segment &g, float3 &oc) {
     oc = make_float3(__fsub_rn(o.x, cell.x), __fsub_rn(o.y, cell.y), __fsub_rn(o.z, cell.z));
     float nb, db;
-    g.next = find_exit(s.faces, cell.begin, cell.end, d, oc, nb, db);
+    g.next = find_exit(s, cell, d, oc, nb, db);
     g.t1 = g.next >= 0 ? __fdiv_rn(nb, db) : __int_as_float(0x7f800000);
     g.a = t0 > tmin ? t0 : tmin;
     g.b = g.t1 < tmax ? g.t1 : tmax;

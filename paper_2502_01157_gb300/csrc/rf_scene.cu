@@ -30,8 +30,9 @@ rf_status cuda_fail(cudaError_t e, const char *what) {
 SceneDev scene_dev(const rf_scene *s) {
     SceneDev d;
     d.cells = s->cells;
-    d.ends = s->off + 1;
     d.faces = s->faces;
+    d.nbr = s->nbr;
+    d.count_bits = s->count_bits;
     d.sh_v8 = s->sh_v8;
     d.density = s->density;
     d.sh = s->sh;
@@ -140,40 +141,54 @@ __device__ __forceinline__ int64_t owner_of(const int32_t *__restrict__ off, int
     return lo;
 }
 
-// One thread per caller edge f of cell i: face record u = 2 (p_j - p_i)/|p_j - p_i|^2
-// at slot poff[i] + (f - off[i]) of the padded list.
-__global__ void pack_faces_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ poff,
+__device__ __forceinline__ void store_face(float4 *__restrict__ faces, int32_t *__restrict__ nbr,
+                                           int64_t g, int l, const float4 &rec) {
+    float *fl = reinterpret_cast<float *>(faces) + 12 * g;
+    fl[l] = rec.x;
+    fl[4 + l] = rec.y;
+    fl[8 + l] = rec.z;
+    nbr[4 * g + l] = __float_as_int(rec.w);
+}
+
+// One thread per caller edge f of cell i (the k-th neighbour): its u goes to
+// lane k % 4 of group goff[i] + k / 4.
+__global__ void pack_faces_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ goff,
                                   const int32_t *__restrict__ idx, const float *__restrict__ pos,
-                                  int64_t n, int64_t e, float4 *__restrict__ faces) {
+                                  int64_t n, int64_t e, float4 *__restrict__ faces,
+                                  int32_t *__restrict__ nbr) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= e) return;
     const int64_t i = owner_of(off, n, f);
-    faces[(int64_t)poff[i] + (f - off[i])] = face_record(pos, i, idx[f]);
+    const int64_t k = f - off[i];
+    store_face(faces, nbr, (int64_t)goff[i] + k / 4, (int)(k % 4), face_record(pos, i, idx[f]));
 }
 
-// Re-pack after the sites moved: neighbour ids come from the existing records.
-__global__ void repack_faces_kernel(const int32_t *__restrict__ poff, const float *__restrict__ pos,
-                                    int64_t n, int64_t slots, float4 *__restrict__ faces) {
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= slots) return;
-    const int32_t j = __float_as_int(faces[f].w);
+// Re-pack after the sites moved: one thread per face slot; the neighbour ids
+// stay, the geometry is recomputed.
+__global__ void repack_faces_kernel(const int32_t *__restrict__ goff, const float *__restrict__ pos,
+                                    int64_t n, int64_t groups, float4 *__restrict__ faces,
+                                    int32_t *__restrict__ nbr) {
+    const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= 4 * groups) return;
+    const int32_t j = nbr[sl];
     if (j < 0) return;  // padding
-    faces[f] = face_record(pos, owner_of(poff, n, f), j);
+    const int64_t g = sl / 4;
+    store_face(faces, nbr, g, (int)(sl % 4), face_record(pos, owner_of(goff, n, g), j));
 }
 
-// Headers and list padding: cell i owns slots [poff[i], poff[i+1]); the caller's
-// count is off[i+1] - off[i]; a slot beyond it is padding {0, 0, 0, -1}.
-__global__ void pack_cells_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ poff,
-                                  const float *__restrict__ pos, int64_t n, float4 *__restrict__ cells,
-                                  float4 *__restrict__ faces) {
+// Headers and group padding: cell i owns groups [goff[i], goff[i+1]); its
+// caller count is off[i+1] - off[i]; the remaining lanes are padding (u = 0).
+__global__ void pack_cells_kernel(const int32_t *__restrict__ off, const int32_t *__restrict__ goff,
+                                  const float *__restrict__ pos, int64_t n, int count_bits,
+                                  float4 *__restrict__ cells, float4 *__restrict__ faces,
+                                  int32_t *__restrict__ nbr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int32_t b = poff[i], e = poff[i + 1];
-    cells[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], __int_as_float(b));
-    if (off) {
-        for (int32_t f = b + (off[i + 1] - off[i]); f < e; ++f)
-            faces[f] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-    }
+    const int32_t gb = goff[i], ge = goff[i + 1];
+    const uint32_t w = ((uint32_t)gb << count_bits) | (uint32_t)(ge - gb);
+    cells[i] = make_float4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], __uint_as_float(w));
+    for (int64_t k = off[i + 1] - off[i]; k < 4 * (int64_t)(ge - gb); ++k)
+        store_face(faces, nbr, gb + k / 4, (int)(k % 4), make_float4(0.f, 0.f, 0.f, __int_as_float(-1)));
 }
 
 __global__ void update_cells_kernel(const float *__restrict__ pos, int64_t n, float4 *__restrict__ cells) {
@@ -277,6 +292,7 @@ static void free_scene(rf_scene *s) {
     cudaFree(s->cells);
     cudaFree(s->off);
     cudaFree(s->faces);
+    cudaFree(s->nbr);
     cudaFree(s->start_keys);
     cudaFree(s->flags);
     delete s;
@@ -354,34 +370,42 @@ RF_API rf_status rf_scene_create(const rf_scene_desc *desc, void *stream, rf_sce
                          "adjacency invalid: %d out-of-range/self, %d asymmetric, %d zero-length edges",
                          flags[1], flags[2], flags[3]));
 
-    // padded lists: each cell's count rounded up to even, so every list starts
-    // at an even slot and faces can be read in 32-byte pairs
-    std::vector<int32_t> off_h(n + 1), poff_h(n + 1);
+    // face groups of four: cell i owns ceil(count / 4) groups; the header
+    // packs its first group and group count into 32 bits
+    std::vector<int32_t> off_h(n + 1), goff_h(n + 1);
     if ((ce = cudaMemcpyAsync(off_h.data(), s->off, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
                               st)) != cudaSuccess ||
         (ce = cudaStreamSynchronize(st)) != cudaSuccess)
         return bail(cuda_fail(ce, "read offsets"));
-    int64_t acc = 0;
-    poff_h[0] = 0;
+    int64_t acc = 0, max_g = 0;
+    goff_h[0] = 0;
     for (int64_t i = 0; i < n; ++i) {
-        const int64_t c = off_h[i + 1] - off_h[i];
-        acc += c + (c & 1);
-        poff_h[i + 1] = (int32_t)acc;
+        const int64_t g = (off_h[i + 1] - off_h[i] + 3) / 4;
+        max_g = g > max_g ? g : max_g;
+        acc += g;
+        goff_h[i + 1] = (int32_t)acc;
     }
-    s->n_slots = acc;
-    RF_TRY_ALLOC(s->faces, sizeof(float4) * (acc > 0 ? acc : 2));
+    int cb = 4;
+    while ((1ll << cb) <= max_g) ++cb;
+    if (acc >= (1ll << (32 - cb)))
+        return bail(fail(RF_ERR_INVALID_ARG, "adjacency too large for the packed header (%lld groups)",
+                         (long long)acc));
+    s->count_bits = cb;
+    s->n_groups = acc;
+    RF_TRY_ALLOC(s->faces, sizeof(float4) * 3 * (acc > 0 ? acc : 1));
+    RF_TRY_ALLOC(s->nbr, sizeof(int32_t) * 4 * (acc > 0 ? acc : 1));
     RF_TRY_ALLOC(s->cells, sizeof(float4) * n);
 #undef RF_TRY_ALLOC
-    if ((ce = cudaMemcpyAsync(s->off, poff_h.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
+    if ((ce = cudaMemcpyAsync(s->off, goff_h.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
                               st)) != cudaSuccess)
-        return bail(cuda_fail(ce, "upload padded offsets"));
+        return bail(cuda_fail(ce, "upload group offsets"));
     if (e > 0) {
         pack_faces_kernel<<<(unsigned)((e + threads - 1) / threads), threads, 0, st>>>(
-            desc->adj_off, s->off, desc->adj_idx, desc->pos, n, e, s->faces);
+            desc->adj_off, s->off, desc->adj_idx, desc->pos, n, e, s->faces, s->nbr);
         if ((ce = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(ce, "pack faces"));
     }
     pack_cells_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
-        desc->adj_off, s->off, desc->pos, n, s->cells, s->faces);
+        desc->adj_off, s->off, desc->pos, n, cb, s->cells, s->faces, s->nbr);
     if ((ce = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(ce, "pack cells"));
 
     bool box_ok = true;
@@ -426,9 +450,9 @@ RF_API rf_status rf_scene_update_positions(rf_scene *s, const float *pos, void *
     // the face records hold the neighbour ids; only the geometry is recomputed
     const int threads = 256;
     cudaStream_t st = (cudaStream_t)stream;
-    if (s->n_slots > 0) {
-        repack_faces_kernel<<<(unsigned)((s->n_slots + threads - 1) / threads), threads, 0, st>>>(
-            s->off, pos, s->n_sites, s->n_slots, s->faces);
+    if (s->n_groups > 0) {
+        repack_faces_kernel<<<(unsigned)((4 * s->n_groups + threads - 1) / threads), threads, 0, st>>>(
+            s->off, pos, s->n_sites, s->n_groups, s->faces, s->nbr);
         RF_CUDA(cudaGetLastError());
     }
     update_cells_kernel<<<(unsigned)((s->n_sites + threads - 1) / threads), threads, 0, st>>>(
