@@ -155,11 +155,18 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int NV = 3 * K;       // SH gradient row
     constexpr int V = NV + 7;       // + density, position of the cell, position of the previous cell
-    constexpr int SP = 33;          // padded stride: conflict-free column and row access
-    __shared__ float stage_all[kBlock / 32][V * SP];
+    constexpr int VP = (V + 3) / 4 * 4;
+    // row stride: a multiple of 4 floats (16-byte row stores) whose quarter is
+    // odd, so the 8 lanes of a 128-bit store phase hit 8 different bank quads;
+    // a column read (one row, consecutive columns) is conflict-free for any stride
+    constexpr int SP = ((VP / 4) % 2 == 1) ? VP : VP + 4;
+    // 32 lane rows + one zero row that pads the 4-member unrolled sums
+    __shared__ __align__(16) float stage_all[kBlock / 32][33 * SP];
     const int lane = threadIdx.x & 31;
     float *stage = stage_all[threadIdx.x >> 5];
     const unsigned full = 0xffffffffu;
+    for (int c = lane; c < SP; c += 32) stage[32 * SP + c] = 0.f;
+    __syncwarp();
 
     // per-lane set-up; no early return: every lane takes part in the
     // warp-wide scatter until the whole warp is done
@@ -368,13 +375,21 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
         }
         if (grouped && leaders) {
             if (shared_row) {
+                // this lane's row: SH gradient, density, position of the cell,
+                // position of the previous cell, zero padding
+                float4 *row = reinterpret_cast<float4 *>(stage + lane * SP);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) stage[q * SP + lane] = cb[q % 3] * Y[q / 3];
-                stage[NV * SP + lane] = sig_bar;
+                for (int q4 = 0; q4 < VP / 4; ++q4) {
+                    float v[4];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    stage[(NV + 1 + a) * SP + lane] = gpos_i[a];
-                    stage[(NV + 4 + a) * SP + lane] = gpos_a[a];
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = 4 * q4 + e;
+                        v[e] = c < NV ? cb[c % 3] * Y[c / 3]
+                             : c == NV ? sig_bar
+                             : c < NV + 4 ? gpos_i[(c - NV - 1) % 3]
+                             : c < NV + 7 ? gpos_a[(c - NV - 4) % 3] : 0.f;
+                    }
+                    row[q4] = make_float4(v[0], v[1], v[2], v[3]);
                 }
             }
             __syncwarp();
@@ -387,10 +402,22 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                 const int cell_a = __shfl_sync(full, key_prev, L);
                 float s0 = 0.f, s1 = 0.f;
                 if (c0 < V) {  // a lane only reads the columns that exist (V may be < 32)
-                    for (unsigned mm = m; mm; mm &= mm - 1) {
-                        const int k = __ffs(mm) - 1;
-                        s0 += stage[c0 * SP + k];
-                        if (c1 < V) s1 += stage[c1 * SP + k];
+                    // four members per pass with independent loads; an absent
+                    // member reads the zero row 32
+                    for (unsigned mm = m; mm;) {
+                        const int k0 = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const int k1 = mm ? __ffs(mm) - 1 : 32;
+                        mm &= mm - 1;
+                        const int k2 = mm ? __ffs(mm) - 1 : 32;
+                        mm &= mm - 1;
+                        const int k3 = mm ? __ffs(mm) - 1 : 32;
+                        mm &= mm - 1;
+                        s0 += (stage[k0 * SP + c0] + stage[k1 * SP + c0]) +
+                              (stage[k2 * SP + c0] + stage[k3 * SP + c0]);
+                        if (c1 < V)
+                            s1 += (stage[k0 * SP + c1] + stage[k1 * SP + c1]) +
+                                  (stage[k2 * SP + c1] + stage[k3 * SP + c1]);
                     }
                 }
 #pragma unroll
