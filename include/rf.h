@@ -357,6 +357,33 @@ RF_API rf_status rf_render_fwd_noalloc(int64_t n_sites, int64_t n_edges, const f
                                        float *depth, void *stream);
 
 /*
+ * Densification and pruning statistics (Sec. 3.3 "Densification",
+ * "Pruning").
+ *
+ * rf_densify_scores: score[i] = |g_pos[i]| * r_i with r_i half the mean
+ *   distance from site i to its Delaunay neighbours (the approximate cell
+ *   radius: the faces lie halfway to the neighbours).  g_pos: device float
+ *   [N][3] (e.g. the accumulated position gradient); score: device float [N].
+ * rf_prune_mask: mask[i] = 1 iff density[i] < threshold and density[j] <
+ *   threshold for every neighbour j (a low-density cell that does not bound a
+ *   denser one).  mask: device uint8 [N]; reads the scene's current
+ *   attributes.
+ * rf_sample_multinomial: m draws of indices in [0, n) with probability
+ *   weights[k] / sum (negative weights count as 0), as in the paper's
+ *   multinomial choice of densification candidates.  u: device float [m],
+ *   uniform numbers in [0, 1) supplied by the caller; a draw takes the first
+ *   k whose inclusive FP64 prefix sum exceeds u * total.  workspace: device,
+ *   8-byte aligned, at least rf_multinomial_workspace_bytes(n) bytes (the
+ *   prefix sums); n <= 16,777,216.  out: device int32 [m].
+ */
+RF_API rf_status rf_densify_scores(rf_scene *scene, const float *g_pos, float *score, void *stream);
+RF_API rf_status rf_prune_mask(rf_scene *scene, float threshold, uint8_t *mask, void *stream);
+RF_API size_t rf_multinomial_workspace_bytes(int64_t n);
+RF_API rf_status rf_sample_multinomial(const float *weights, int64_t n, const float *u, int64_t m,
+                                       void *workspace, size_t workspace_bytes, int32_t *out,
+                                       void *stream);
+
+/*
  * MSE loss helper for a training step (device, n = 3 * rays):
  *   d_rgb[k] = 2 * scale * (rgb[k] - target[k]);  *loss += scale * sum_k (rgb[k]-target[k])^2
  * loss is a device float accumulated with atomics (zero it first).

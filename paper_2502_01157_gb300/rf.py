@@ -127,6 +127,11 @@ SIGNATURES = {
     "rf_serve_stats": (_S, [_P, ctypes.POINTER(rf_serve_metrics)]),
     "rf_serve_reset_stats": (_S, [_P]),
     "rf_serve_destroy": (_S, [_P]),
+    "rf_densify_scores": (_S, [_P, _P, _P, _P]),
+    "rf_prune_mask": (_S, [_P, ctypes.c_float, _P, _P]),
+    "rf_multinomial_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "rf_sample_multinomial": (_S, [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_size_t, _P,
+                                   _P]),
     "rf_render_fwd_noalloc": (_S, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
                                    ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(rf_camera), ctypes.c_int32,
@@ -359,6 +364,19 @@ class Foam:
                                     _ptr(cells), _ptr(counts), _stream(stream)))
         return cells, counts
 
+    def densify_scores(self, g_pos, stream=None):
+        """|dL/dp_i| * (half the mean distance to the Delaunay neighbours), [N]."""
+        score = torch.empty(self.n_sites, device=self.pos.device)
+        _check(lib().rf_densify_scores(self.handle, _ptr(g_pos.contiguous().float()), _ptr(score),
+                                       _stream(stream)))
+        return score
+
+    def prune_mask(self, threshold: float, stream=None):
+        """Sites whose density and all neighbours' densities are below ``threshold``."""
+        mask = torch.empty(self.n_sites, dtype=torch.uint8, device=self.pos.device)
+        _check(lib().rf_prune_mask(self.handle, float(threshold), _ptr(mask), _stream(stream)))
+        return mask.bool()
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().rf_scene_destroy(self._h)
@@ -369,6 +387,20 @@ class Foam:
             self.close()
         except Exception:
             pass
+
+
+def sample_multinomial(weights, u, stream=None):
+    """Indices drawn with probability proportional to ``weights`` (device
+    float [n]); ``u``: device float [m] of uniform numbers in [0, 1)."""
+    w = weights.contiguous().float()
+    uu = u.contiguous().float()
+    n = w.numel()
+    nbytes = int(lib().rf_multinomial_workspace_bytes(n))
+    ws = torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=w.device)
+    out = torch.empty(uu.numel(), dtype=torch.int32, device=w.device)
+    _check(lib().rf_sample_multinomial(_ptr(w), n, _ptr(uu), uu.numel(), _ptr(ws), nbytes,
+                                       _ptr(out), _stream(stream)))
+    return out
 
 
 def mse_grad(rgb, target, scale: float, loss=None, stream=None):
