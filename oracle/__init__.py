@@ -8,8 +8,8 @@ The arithmetic lives in ``rf_oracle.c`` (plain C, FP64, OpenMP over rays); this
 module compiles it with gcc on first use and marshals numpy arrays.  Every
 function follows the paper's statement of the method:
 
-* :func:`camera_rays`  -- pinhole rays through pixel centres (the inputs o, d
-  of Alg. 1).
+* :func:`camera_rays`  -- pinhole or equidistant-fisheye rays through pixel
+  centres, with an optional rolling shutter (the inputs o, d of Alg. 1).
 * :func:`nearest_site` -- nn(o), the initial cell of Alg. 1.
 * :func:`render`       -- Alg. 1 with Eq. (3)-(4) compositing (Sec. 3.1-3.2).
 * :func:`render_bwd`   -- reverse-mode gradient of the rendered outputs; sites
@@ -73,14 +73,14 @@ def lib():
             L.orc_render.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int, _d,
                                      _d, ctypes.c_int64, _i64, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_double, _d, _d, _d, _i32, _u8, _u8, ctypes.c_int,
-                                     _i32, _d, ctypes.c_int]
+                                     _i32, _d, _d, ctypes.c_int]
             L.orc_render.restype = ctypes.c_int
             L.orc_render_bwd.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int, _d,
                                          _d, ctypes.c_int64, _i64, ctypes.c_double, ctypes.c_int,
-                                         _d, _d, _d, _d, _d, _d, _d, ctypes.c_int]
+                                         _d, _d, _d, _d, _d, _d, _d, _d, ctypes.c_int]
             L.orc_render_quantile.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int,
                                               _d, _d, ctypes.c_int64, _i64, ctypes.c_double,
-                                              ctypes.c_int, _d, ctypes.c_int]
+                                              ctypes.c_int, _d, _d, ctypes.c_int]
             L.orc_render_quantile.restype = ctypes.c_int
             L.orc_render_bwd.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
@@ -102,7 +102,17 @@ def _f64(a):
 
 
 def _cam(cam) -> np.ndarray:
-    return _f64(cam.as_f64() if hasattr(cam, "as_f64") else cam)
+    c = _f64(cam.as_f64() if hasattr(cam, "as_f64") else cam)
+    if len(c) == 20:  # pinhole, global shutter
+        c = np.concatenate([c, np.zeros(4)])
+    return c
+
+
+def _fx(effects):
+    """Sphere effect as 6 doubles {max_bounces, centre, radius, ior}, or None."""
+    if effects is None:
+        return None
+    return _f64(effects.as_f64() if hasattr(effects, "as_f64") else effects)
 
 
 def default_tau(scene, cam) -> float:
@@ -157,10 +167,12 @@ def nearest_site(pos, q):
 
 
 def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
-           tau=None, trace: int = 0, threads: int = 0) -> dict:
+           tau=None, trace: int = 0, threads: int = 0, effects=None) -> dict:
     """Forward render (Alg. 1, Eq. 3-4).  Returns rgb [R,3], trans [R], depth [R],
     steps [R], status [R], degen [R] and, if ``trace > 0``, trace_cells
-    [R,trace] (-1 padded) and trace_t [R,trace]."""
+    [R,trace] (-1 padded) and trace_t [R,trace].  ``effects``: an analytic
+    sphere the rays reflect off or refract through (``scenes.Sphere``)."""
+    fx = _fx(effects)
     S = _SceneF64(scene)
     c = _cam(cam)
     n_all = int(c[16]) * int(c[17])
@@ -179,7 +191,7 @@ def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
                           _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d), R, _p(px, _i64),
                           float(eps), int(max_steps), tau, _p(rgb, _d), _p(tr, _d), _p(dp, _d),
                           _p(st, _i32), _p(ss, _u8), _p(dg, _u8), int(trace), _p(tc, _i32),
-                          _p(tt, _d), int(threads))
+                          _p(tt, _d), _p(fx, _d), int(threads))
     if rc:
         raise ValueError("oracle render: bad arguments")
     out = dict(rgb=rgb, trans=tr, depth=dp, steps=st, status=ss, degen=dg.astype(bool), tau=tau)
@@ -190,9 +202,10 @@ def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
 
 
 def render_quantile(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
-                    threads: int = 0) -> np.ndarray:
+                    threads: int = 0, effects=None) -> np.ndarray:
     """Quantile loss of Eq. (6) per ray: E|W^-1(u1) - W^-1(u2)|, u1, u2 ~ U[0,1],
     W^-1 the quantile function of the ray's normalised weight distribution."""
+    fx = _fx(effects)
     S = _SceneF64(scene)
     c = _cam(cam)
     n_all = int(c[16]) * int(c[17])
@@ -202,17 +215,19 @@ def render_quantile(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int =
     rc = lib().orc_render_quantile(S.n, _p(S.pos, _d), _p(S.off, _i64), _p(S.adj, _i32),
                                    _p(S.sigma, _d), _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d),
                                    R, _p(px, _i64), float(eps), int(max_steps), _p(q, _d),
-                                   int(threads))
+                                   _p(fx, _d), int(threads))
     if rc:
         raise ValueError("oracle render_quantile: bad arguments")
     return q
 
 
 def render_bwd(scene, cam, g_rgb, g_trans=None, g_depth=None, pixels=None, eps: float = 1e-4,
-               max_steps: int = 1 << 16, threads: int = 0, g_quantile=None) -> dict:
+               max_steps: int = 1 << 16, threads: int = 0, g_quantile=None,
+               effects=None) -> dict:
     """Gradient of sum(g_rgb*rgb) + sum(g_trans*trans) + sum(g_depth*depth)
     + sum(g_quantile*quantile) with respect to density [N], SH [N,K,3] and
     positions [N,3]."""
+    fx = _fx(effects)
     S = _SceneF64(scene)
     c = _cam(cam)
     n_all = int(c[16]) * int(c[17])
@@ -230,7 +245,7 @@ def render_bwd(scene, cam, g_rgb, g_trans=None, g_depth=None, pixels=None, eps: 
                               _p(S.sigma, _d), _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d), R,
                               _p(px, _i64), float(eps), int(max_steps), _p(gr, _d), _p(gt, _d),
                               _p(gd, _d), _p(gq, _d), _p(g_sigma, _d), _p(g_sh, _d), _p(g_pos, _d),
-                              int(threads))
+                              _p(fx, _d), int(threads))
     if rc:
         raise ValueError("oracle render_bwd: bad arguments")
     return dict(density=g_sigma, sh=g_sh, pos=g_pos)

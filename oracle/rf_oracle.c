@@ -9,8 +9,11 @@
  *
  * What it computes (all in FP64, one ray at a time, in the paper's order):
  *
- *   - Ray generation for a pinhole camera (pixel centres, OpenCV frame).
- *   - The initial cell nn(o): the site nearest to the ray origin (Alg. 1).
+ *   - Ray generation for a pinhole or equidistant-fisheye camera (pixel
+ *     centres, OpenCV frame), optionally with a rolling shutter that moves
+ *     each row's origin (the ray-based effects figure, Fig. 2).
+ *   - The initial cell nn(o): the site nearest to the ray origin (Alg. 1),
+ *     per row for a rolling shutter.
  *   - The walk of Alg. 1 (Sec. 3.2): in cell i, over every neighbour j in
  *     N(i), intersect the ray with the bisector plane of x_i and x_j; a plane
  *     whose normal x_j - x_i makes an angle below 90 deg with d is an exit
@@ -18,6 +21,10 @@
  *     gives t_1 and the next cell.
  *   - Piecewise-constant compositing, Eq. (3)-(4): alpha = 1 - exp(-sigma
  *     delta), C += T alpha c, T *= (1 - alpha), while T > eps.
+ *   - Optionally one analytic sphere met in the same walk (Fig. 2): a
+ *     mirror, or clear glass with Snell refraction and total internal
+ *     reflection; the ray bends at the hit point and the walk carries on in
+ *     the same cell along the new direction.
  *   - Colour from real spherical harmonics of degree <= 3 in the ray
  *     direction, plus 0.5, clamped at 0 (Sec. 3.4 "Training").
  *   - The quantile loss of Eq. (6): the expected distance between two
@@ -109,24 +116,39 @@ int orc_sh_basis_batch(int degree, int64_t n, const double *dirs, double *Y)
 
 /* ------------------------------------------------------------------------ */
 /* Camera: cam[0..11] = c2w (3x4 row-major [R|t]), cam[12..15] = fx fy cx cy, */
-/* cam[16..17] = width height, cam[18..19] = t_near t_far.                    */
+/* cam[16..17] = width height, cam[18..19] = t_near t_far, cam[20] = model    */
+/* (0 pinhole, 1 equidistant fisheye), cam[21..23] = rolling-shutter          */
+/* velocity (the centre moves by it from the first row to the last).          */
 /* Pixel p = v * width + u; its ray passes through the pixel centre.          */
 /* ------------------------------------------------------------------------ */
 void orc_camera_ray(const double *cam, int64_t pixel, double *o, double *d)
 {
     const int64_t W = (int64_t)cam[16];
+    const int64_t H = (int64_t)cam[17];
     const int64_t u = pixel % W, v = pixel / W;
-    const double xc = ((double)u + 0.5 - cam[14]) / cam[12];
-    const double yc = ((double)v + 0.5 - cam[15]) / cam[13];
-    const double zc = 1.0;
+    const double x = ((double)u + 0.5 - cam[14]) / cam[12];
+    const double y = ((double)v + 0.5 - cam[15]) / cam[13];
+    double xc = x, yc = y, zc = 1.0;
+    if ((int)cam[20] == 1) {
+        /* equidistant fisheye: the angle from the optical axis equals the
+         * radius in normalised image coordinates */
+        const double th = sqrt(x * x + y * y);
+        const double sc = th > 0.0 ? sin(th) / th : 1.0;
+        xc = x * sc;
+        yc = y * sc;
+        zc = cos(th);
+    }
+    const double row = ((double)v + 0.5) / (double)H - 0.5;
     double w[3];
     for (int r = 0; r < 3; ++r) {
         w[r] = cam[4 * r + 0] * xc + cam[4 * r + 1] * yc + cam[4 * r + 2] * zc;
-        o[r] = cam[4 * r + 3];
+        o[r] = cam[4 * r + 3] + row * cam[21 + r];
     }
     const double len = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     for (int r = 0; r < 3; ++r) d[r] = w[r] / len;
 }
+
+static int has_shutter(const double *cam) { return cam[21] != 0.0 || cam[22] != 0.0 || cam[23] != 0.0; }
 
 /* Nearest site (lowest index on exact ties); *gap receives the distance from
  * q to the bisector plane of its two nearest sites (HUGE_VAL if N < 2). */
@@ -192,11 +214,84 @@ typedef struct {
 
 typedef struct {
     int64_t cell, next;   /* next = -1: no exit */
-    double t0, t1;        /* raw entry / exit parameters */
+    double t0, t1;        /* raw entry / exit parameters (t1: the sphere hit if bounce) */
     double a, b;          /* composited part [a,b] (a >= b: nothing) */
     double delta, sigma, e, T;   /* T: transmittance before the segment */
     double pre[3], c[3];  /* colour before / after the clamp at 0 */
+    double o[3], d[3];    /* the ray this segment lies on */
+    double tmin, tmax;    /* that ray's compositing interval */
+    double soff;          /* path length before that ray's origin (bounces) */
+    int bounce;           /* the segment ends on the sphere, not on a face */
 } seg_t;
+
+/* Optional analytic sphere the rays bounce off (mirror) or through (clear
+ * glass, Snell's law with total internal reflection): fx = {max_bounces,
+ * cx, cy, cz, radius, ior}, ior = 0 for a mirror. */
+typedef struct {
+    int max_bounces;
+    double c[3], r, ior;
+} effects_t;
+
+static int effects_of(const double *fx, effects_t *E)
+{
+    if (!fx || !(fx[4] > 0.0) || fx[0] < 1.0) return 0;
+    E->max_bounces = (int)fx[0];
+    for (int a = 0; a < 3; ++a) E->c[a] = fx[1 + a];
+    E->r = fx[4];
+    E->ior = fx[5];
+    return 1;
+}
+
+/* Parameter of the next sphere crossing of the ray: the entry (near root)
+ * from outside, the exit (far root) from inside; HUGE_VAL if none ahead.
+ * *disc_out returns the discriminant relative to r^2 (tangency test). */
+static double sphere_hit(const effects_t *E, const double *o, const double *d, int inside,
+                         double *disc_out)
+{
+    double oc[3], b = 0.0, cc = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        oc[a] = o[a] - E->c[a];
+        b += d[a] * oc[a];
+        cc += oc[a] * oc[a];
+    }
+    cc -= E->r * E->r;
+    const double disc = b * b - cc;
+    *disc_out = disc / (E->r * E->r);
+    if (disc < 0.0) return HUGE_VAL;
+    const double t = inside ? -b + sqrt(disc) : -b - sqrt(disc);
+    return t > 0.0 ? t : HUGE_VAL;
+}
+
+/* New direction at the hit point p: mirror reflection, or refraction with
+ * relative index n1/n2 (total internal reflection when impossible).
+ * Returns 1 if the ray crossed into the other side. *kout: Snell's k. */
+static int sphere_bounce(const effects_t *E, const double *p, double *d, int inside, double *kout)
+{
+    double n[3], dn = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        n[a] = (p[a] - E->c[a]) / E->r;
+        dn += d[a] * n[a];
+    }
+    *kout = 1.0;
+    int crossed = 0;
+    if (E->ior > 0.0) {
+        const double sgn = inside ? -1.0 : 1.0;  /* normal on the incoming side */
+        const double eta = inside ? E->ior : 1.0 / E->ior;
+        const double cosi = -dn * sgn;
+        const double k = 1.0 - eta * eta * (1.0 - cosi * cosi);
+        *kout = k;
+        if (k >= 0.0) {
+            const double f = eta * cosi - sqrt(k);
+            for (int a = 0; a < 3; ++a) d[a] = eta * d[a] + f * sgn * n[a];
+            crossed = 1;
+        }
+    }
+    if (!crossed)
+        for (int a = 0; a < 3; ++a) d[a] -= 2.0 * dn * n[a];
+    const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int a = 0; a < 3; ++a) d[a] /= len;
+    return crossed;
+}
 
 typedef struct {
     seg_t *s;
@@ -247,14 +342,20 @@ typedef struct {
  * Alg. 1 for one ray.  Segments are appended to L (if non-NULL); the visited
  * cells and raw exit parameters to trace_cells / trace_t (up to max_trace).
  */
-static void render_ray(const scene_t *S, int64_t start, const double *o, const double *d,
+static void render_ray(const scene_t *S, int64_t start, const double *o_in, const double *d_in,
                        double tmin, double tmax, double eps, int max_steps, double tau,
-                       const double *Y, ray_out_t *R, seglist_t *L,
-                       int max_trace, int32_t *trace_cells, double *trace_t)
+                       double *Y, ray_out_t *R, seglist_t *L,
+                       int max_trace, int32_t *trace_cells, double *trace_t, const effects_t *E)
 {
-    double T = 1.0, C[3] = {0.0, 0.0, 0.0}, D = 0.0, t0 = 0.0;
+    double T = 1.0, C[3] = {0.0, 0.0, 0.0}, D = 0.0, t0 = 0.0, s_off = 0.0;
+    double o[3] = {o_in[0], o_in[1], o_in[2]}, d[3] = {d_in[0], d_in[1], d_in[2]};
     int64_t i = start;
-    int steps = 0;
+    int steps = 0, bounces = 0, inside = 0;
+    if (E) {
+        double r2 = 0.0;
+        for (int a = 0; a < 3; ++a) r2 += (o[a] - E->c[a]) * (o[a] - E->c[a]);
+        inside = r2 < E->r * E->r;
+    }
     R->status = ORC_RAY_OK;
     while (T > eps) {
         if (fabs(T - eps) <= 1e-3 * eps) R->degen = 1;
@@ -278,39 +379,68 @@ static void render_ray(const scene_t *S, int64_t start, const double *o, const d
                 if (t < t1) { t1 = t; nxt = j; }
             }
         }
+        /* does the ray meet the sphere inside this cell? */
+        int hit = 0;
+        double ts = HUGE_VAL;
+        if (E && bounces < E->max_bounces) {
+            double disc;
+            ts = sphere_hit(E, o, d, inside, &disc);
+            if (fabs(disc) < 1e-6) R->degen = 1;  /* grazing: hit or miss is a tie */
+            hit = ts >= t0 && ts < t1 && ts < tmax;
+        }
+        const double tend = hit ? ts : t1;
         /* degeneracy test at the step's end point */
         {
-            const double te = (nxt >= 0 && t1 < tmax) ? t1 : tmax;
+            const double te = (hit || (nxt >= 0 && t1 < tmax)) ? tend : tmax;
             double p[3];
             for (int a = 0; a < 3; ++a) p[a] = o[a] + te * d[a];
             for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
                 const int64_t k = S->adj[f];
-                if (k == nxt && te == t1) continue;
+                if (!hit && k == nxt && te == t1) continue;
                 if (plane_dist(S, i, k, p) < tau) { R->degen = 1; break; }
             }
         }
         seg_t s;
         s.cell = i;
-        s.next = nxt;
+        s.next = hit ? i : nxt;
+        s.bounce = hit;
         s.t0 = t0;
-        s.t1 = t1;
+        s.t1 = tend;
         s.a = t0 > tmin ? t0 : tmin;
-        s.b = t1 < tmax ? t1 : tmax;
+        s.b = tend < tmax ? tend : tmax;
         s.delta = s.b > s.a ? s.b - s.a : 0.0;
         s.sigma = S->sigma[i];
         s.e = exp(-s.sigma * s.delta);
         s.T = T;
+        s.tmin = tmin;
+        s.tmax = tmax;
+        s.soff = s_off;
+        for (int a = 0; a < 3; ++a) { s.o[a] = o[a]; s.d[a] = d[a]; }
         cell_colour(S, i, Y, s.pre, s.c);
         const double alpha = 1.0 - s.e;
         for (int ch = 0; ch < 3; ++ch) C[ch] += T * alpha * s.c[ch];
-        D += T * alpha * 0.5 * (s.a + s.b);
+        D += T * alpha * (s_off + 0.5 * (s.a + s.b));
         T *= s.e;
         seg_push(L, &s);
         if (steps < max_trace) {
             trace_cells[steps] = (int32_t)i;
-            trace_t[steps] = t1;
+            trace_t[steps] = tend;
         }
         ++steps;
+        if (hit) {
+            /* bounce: the new ray starts at the hit point, in the same cell */
+            double p[3], k;
+            for (int a = 0; a < 3; ++a) p[a] = o[a] + ts * d[a];
+            if (sphere_bounce(E, p, d, inside, &k)) inside = !inside;
+            if (E->ior > 0.0 && fabs(k) < 1e-6) R->degen = 1;  /* at the critical angle */
+            for (int a = 0; a < 3; ++a) o[a] = p[a];
+            s_off += ts;
+            t0 = 0.0;
+            ++bounces;
+            orc_sh_basis(S->deg, d, Y);
+            if (!ray_interval(o, d, S->box, 0.0, 0.0, &tmin, &tmax)) break;
+            continue;
+        }
         if (nxt < 0 || t1 >= tmax) break;
         if (t1 > t0) t0 = t1;
         i = nxt;
@@ -413,6 +543,36 @@ static int setup_scene(scene_t *S, int64_t n, const double *pos, const int64_t *
     return 0;
 }
 
+/* Start cell of Alg. 1: nn(o).  All rays of a global-shutter camera share
+ * one origin; a rolling shutter gives every row its own. */
+typedef struct {
+    int64_t start;
+    int degen;
+} cam_start_t;
+
+static cam_start_t camera_start(const scene_t *S, const double *cam, double tau)
+{
+    const double o[3] = {cam[3], cam[7], cam[11]};  /* the centre (mid-frame for a rolling shutter) */
+    double gap;
+    cam_start_t c;
+    c.start = orc_nearest_site(S->n, S->pos, o, &gap);
+    c.degen = gap < tau;
+    return c;
+}
+
+static int64_t ray_start(const scene_t *S, const double *cam, const cam_start_t *c,
+                         const double *ro, double tau, int *degen)
+{
+    if (!has_shutter(cam)) {
+        if (c->degen) *degen = 1;
+        return c->start;
+    }
+    double gap;
+    const int64_t s = orc_nearest_site(S->n, S->pos, ro, &gap);
+    if (gap < tau) *degen = 1;
+    return s;
+}
+
 /*
  * Forward render of n_rays pixels of one camera (pixels == NULL: all pixels
  * in order).  Outputs per ray: rgb[3], trans, depth, steps, status, degen.
@@ -425,15 +585,13 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
                double eps, int max_steps, double tau,
                double *rgb, double *trans, double *depth, int32_t *steps, uint8_t *status,
                uint8_t *degen, int max_trace, int32_t *trace_cells, double *trace_t,
-               int n_threads)
+               const double *effects, int n_threads)
 {
     scene_t S;
     if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
-    double o[3], dummy[3];
-    orc_camera_ray(cam, 0, o, dummy);
-    double gap;
-    const int64_t start = orc_nearest_site(n_sites, pos, o, &gap);
-    const int cam_degen = gap < tau;
+    effects_t E;
+    const effects_t *EP = effects_of(effects, &E) ? &E : NULL;
+    const cam_start_t cs = camera_start(&S, cam, tau);
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 64)
@@ -448,11 +606,13 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
         R.T = 1.0;
         int32_t *tc = max_trace > 0 ? trace_cells + r * (int64_t)max_trace : NULL;
         double *tt = max_trace > 0 ? trace_t + r * (int64_t)max_trace : NULL;
+        int sdeg = 0;
+        const int64_t start = ray_start(&S, cam, &cs, ro, tau, &sdeg);
         if (ray_interval(ro, rd, box, cam[18], cam[19], &tmin, &tmax)) {
             render_ray(&S, start, ro, rd, tmin, tmax, eps, max_steps, tau, Y, &R, NULL,
-                       max_trace, tc, tt);
+                       max_trace, tc, tt, EP);
         }
-        if (cam_degen) R.degen = 1;
+        if (sdeg) R.degen = 1;
         for (int ch = 0; ch < 3; ++ch) rgb[3 * r + ch] = R.rgb[ch];
         trans[r] = R.T;
         depth[r] = R.depth;
@@ -467,13 +627,13 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
 int orc_render_quantile(int64_t n_sites, const double *pos, const int64_t *off, const int32_t *adj,
                         const double *sigma, const double *sh, int sh_degree, const double *box,
                         const double *cam, int64_t n_rays, const int64_t *pixels, double eps,
-                        int max_steps, double *quantile, int n_threads)
+                        int max_steps, double *quantile, const double *effects, int n_threads)
 {
     scene_t S;
     if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
-    double o[3], dummy[3];
-    orc_camera_ray(cam, 0, o, dummy);
-    const int64_t start = orc_nearest_site(n_sites, pos, o, NULL);
+    effects_t E;
+    const effects_t *EP = effects_of(effects, &E) ? &E : NULL;
+    const cam_start_t cs = camera_start(&S, cam, -1.0);
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 64)
@@ -485,10 +645,13 @@ int orc_render_quantile(int64_t n_sites, const double *pos, const int64_t *off, 
         orc_sh_basis(S.deg, rd, Y);
         quantile[r] = 0.0;
         if (!ray_interval(ro, rd, box, cam[18], cam[19], &tmin, &tmax)) continue;
+        int sdeg = 0;
+        const int64_t start = ray_start(&S, cam, &cs, ro, -1.0, &sdeg);
         ray_out_t R;
         memset(&R, 0, sizeof R);
         seglist_t L = {NULL, 0, 0};
-        render_ray(&S, start, ro, rd, tmin, tmax, eps, max_steps, -1.0, Y, &R, &L, 0, NULL, NULL);
+        render_ray(&S, start, ro, rd, tmin, tmax, eps, max_steps, -1.0, Y, &R, &L, 0, NULL, NULL,
+                   EP);
         quantile[r] = quantile_loss(&L, R.T);
         free(L.s);
     }
@@ -514,13 +677,13 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
                    double eps, int max_steps,
                    const double *g_rgb, const double *g_trans, const double *g_depth,
                    const double *g_quantile, double *g_sigma, double *g_sh, double *g_pos,
-                   int n_threads)
+                   const double *effects, int n_threads)
 {
     scene_t S;
     if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
-    double o[3], dummy[3];
-    orc_camera_ray(cam, 0, o, dummy);
-    const int64_t start = orc_nearest_site(n_sites, pos, o, NULL);
+    effects_t E;
+    const effects_t *EP = effects_of(effects, &E) ? &E : NULL;
+    const cam_start_t cs = camera_start(&S, cam, -1.0);
     const int K = S.K;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -532,11 +695,13 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
         orc_camera_ray(cam, px, ro, rd);
         orc_sh_basis(S.deg, rd, Y);
         if (!ray_interval(ro, rd, box, cam[18], cam[19], &tmin, &tmax)) continue;
+        int sdeg = 0;
+        const int64_t start = ray_start(&S, cam, &cs, ro, -1.0, &sdeg);
         ray_out_t R;
         memset(&R, 0, sizeof R);
         seglist_t L = {NULL, 0, 0};
         render_ray(&S, start, ro, rd, tmin, tmax, eps, max_steps, -1.0, Y, &R,
-                   &L, 0, NULL, NULL);
+                   &L, 0, NULL, NULL, EP);
         const double gC[3] = {g_rgb[3 * r], g_rgb[3 * r + 1], g_rgb[3 * r + 2]};
         const double gT = g_trans ? g_trans[r] : 0.0;
         const double gD = g_depth ? g_depth[r] : 0.0;
@@ -549,7 +714,7 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
         for (int64_t k = L.n - 1; k >= 0; --k) {
             const seg_t *s = &L.s[k];
             const double w = s->T * (1.0 - s->e);
-            const double z = 0.5 * (s->a + s->b);
+            const double z = s->soff + 0.5 * (s->a + s->b);
             double wbar = gD * z;
             for (int ch = 0; ch < 3; ++ch) wbar += gC[ch] * s->c[ch];
             /* T_{k+1} = T_k e_k;  C += T_k (1 - e_k) c_k;  D += T_k (1 - e_k) z_k */
@@ -560,15 +725,19 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
             const double zbar = gD * w;
             double abar = 0.5 * zbar, bbar = 0.5 * zbar;
             if (s->b > s->a) { bbar += dbar; abar -= dbar; }
-            double t1bar = (s->t1 < tmax) ? bbar : 0.0;
-            double t0bar = (s->t0 > tmin) ? abar : 0.0;
-            /* t0 of segment k+1 = max(t0_k, t1_k) */
-            if (k + 1 < L.n) {
+            double t1bar = (s->t1 < s->tmax) ? bbar : 0.0;
+            double t0bar = (s->t0 > s->tmin) ? abar : 0.0;
+            /* t0 of segment k+1 = max(t0_k, t1_k); a bounce restarts at t0 = 0
+             * on a new ray, and the sphere hit itself does not move with the
+             * sites */
+            if (s->bounce) t1bar = 0.0;
+            else if (k + 1 < L.n) {
                 if (s->t1 >= s->t0) t1bar += t0bar_next;
                 else t0bar += t0bar_next;
             }
             t0bar_next = t0bar;
             const int64_t i = s->cell;
+            orc_sh_basis(S.deg, s->d, Y);
             ORC_ATOMIC
             g_sigma[i] += sigbar;
             for (int ch = 0; ch < 3; ++ch) {
@@ -585,8 +754,8 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
                 const int64_t j = s->next;
                 double den = 0.0, p[3];
                 for (int a = 0; a < 3; ++a) {
-                    den += (pos[3 * j + a] - pos[3 * i + a]) * rd[a];
-                    p[a] = ro[a] + s->t1 * rd[a];
+                    den += (pos[3 * j + a] - pos[3 * i + a]) * s->d[a];
+                    p[a] = s->o[a] + s->t1 * s->d[a];
                 }
                 for (int a = 0; a < 3; ++a) {
                     const double gj = t1bar * (pos[3 * j + a] - p[a]) / den;

@@ -45,13 +45,17 @@ _GLOBAL_DELAUNAY_MAX = 250_000
 # ----------------------------------------------------------------------------
 @dataclasses.dataclass
 class Camera:
-    """Pinhole camera.
+    """Pinhole or equidistant-fisheye camera, global or rolling shutter.
 
     ``c2w`` is a 3x4 row-major matrix [R | t]: a point ``x_c`` in the camera
     frame (OpenCV: +x right, +y down, +z forward) maps to ``R @ x_c + t`` in the
     world; ``t`` is the camera centre.  Intrinsics are in pixels.  ``t_near`` and
     ``t_far`` bound the rendered depth along each unit ray (``t_far <= 0``: no
-    bound beyond the scene box).
+    bound beyond the scene box).  ``model``: ``PINHOLE`` or ``FISHEYE``
+    (equidistant: the angle to the optical axis equals the normalised image
+    radius).  ``shutter``: world-space displacement of the centre from the first
+    image row to the last (rolling shutter); row ``v`` is exposed from
+    ``t + ((v + 1/2)/height - 1/2) * shutter``.
     """
 
     c2w: np.ndarray
@@ -63,6 +67,11 @@ class Camera:
     height: int
     t_near: float = 0.0
     t_far: float = 0.0
+    model: int = 0
+    shutter: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+
+    PINHOLE = 0
+    FISHEYE = 1
 
     def __post_init__(self):
         self.c2w = np.asarray(self.c2w, dtype=np.float32).reshape(3, 4)
@@ -71,16 +80,52 @@ class Camera:
             setattr(self, f, float(np.float32(getattr(self, f))))
         self.width = int(self.width)
         self.height = int(self.height)
+        self.model = int(self.model)
+        self.shutter = tuple(float(v) for v in np.asarray(self.shutter, np.float32).reshape(3))
 
     @property
     def n_rays(self) -> int:
         return self.width * self.height
 
     def as_f64(self) -> np.ndarray:
-        """20 doubles: c2w(12), fx, fy, cx, cy, width, height, t_near, t_far."""
+        """24 doubles: c2w(12), fx, fy, cx, cy, width, height, t_near, t_far,
+        model, shutter(3)."""
         return np.array(list(self.c2w.reshape(-1).astype(np.float64)) +
                         [self.fx, self.fy, self.cx, self.cy, self.width,
-                         self.height, self.t_near, self.t_far], dtype=np.float64)
+                         self.height, self.t_near, self.t_far, self.model] +
+                        list(self.shutter), dtype=np.float64)
+
+
+def fisheye(width: int, height: int, fov_deg: float, c2w=None) -> Camera:
+    """Equidistant fisheye whose image circle of diameter ``min(width,
+    height)`` spans ``fov_deg`` (up to 360)."""
+    f = (min(width, height) / 2.0) / math.radians(fov_deg / 2.0)
+    if c2w is None:
+        c2w = np.concatenate([np.eye(3), np.zeros((3, 1))], axis=1)
+    return Camera(c2w, f, f, width / 2.0, height / 2.0, width, height, model=Camera.FISHEYE)
+
+
+@dataclasses.dataclass
+class Sphere:
+    """Analytic sphere in the foam: a perfect mirror (``ior == 0``) or clear
+    glass of refractive index ``ior`` (Snell refraction, total internal
+    reflection).  A ray interacts with it at most ``max_bounces`` times and
+    then passes through it."""
+
+    centre: Tuple[float, float, float]
+    radius: float
+    ior: float = 0.0
+    max_bounces: int = 8
+
+    def __post_init__(self):
+        self.centre = tuple(float(v) for v in np.asarray(self.centre, np.float32).reshape(3))
+        self.radius = float(np.float32(self.radius))
+        self.ior = float(np.float32(self.ior))
+        self.max_bounces = int(self.max_bounces)
+
+    def as_f64(self) -> np.ndarray:
+        """6 doubles: max_bounces, centre(3), radius, ior."""
+        return np.array([self.max_bounces, *self.centre, self.radius, self.ior], np.float64)
 
 
 def pinhole(width: int, height: int, fov_y_deg: float, c2w=None,
