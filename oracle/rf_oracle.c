@@ -362,21 +362,22 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
         if (steps >= max_steps) { R->status = ORC_RAY_MAX_STEPS; break; }
         const double *x = S->pos + 3 * i;
         /* nearest front-facing bisector plane (Fig. 3) */
-        double t1 = HUGE_VAL;
+        double t1 = HUGE_VAL, cos_exit = 1.0;
         int64_t nxt = -1;
         for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
             const int64_t j = S->adj[f];
             const double *xp = S->pos + 3 * j;
-            double den = 0.0, num = 0.0;
+            double den = 0.0, num = 0.0, nn = 0.0;
             for (int a = 0; a < 3; ++a) {
                 const double n = xp[a] - x[a];
                 const double m = 0.5 * (xp[a] + x[a]);
                 den += n * d[a];
                 num += n * (m - o[a]);
+                nn += n * n;
             }
             if (den > 0.0) {
                 const double t = num / den;
-                if (t < t1) { t1 = t; nxt = j; }
+                if (t < t1) { t1 = t; nxt = j; cos_exit = den / sqrt(nn); }
             }
         }
         /* does the ray meet the sphere inside this cell? */
@@ -395,6 +396,10 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
             }
         }
         const double tend = hit ? ts : t1;
+        /* a crossing at grazing incidence: its point on the face moves by
+         * ~ (direction error) / cos along the face, so its gradient is
+         * ill-conditioned in any working precision */
+        if (!hit && nxt >= 0 && t1 < tmax && cos_exit < 1e-3) R->degen = 1;
         /* degeneracy test at the step's end point */
         {
             const double te = (hit || (nxt >= 0 && t1 < tmax)) ? tend : tmax;
