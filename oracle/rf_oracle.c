@@ -386,7 +386,9 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
         if (E && bounces < E->max_bounces) {
             double disc;
             ts = sphere_hit(E, o, d, inside, &disc);
-            if (fabs(disc) < 1e-4) R->degen = 1;  /* grazing: hit or miss is a near tie */
+            /* near-grazing: the hit point's error grows as 1/sqrt(disc), so the
+             * bent direction (and all that follows) is ill-conditioned */
+            if (fabs(disc) < 1e-2) R->degen = 1;
             hit = ts >= t0 && ts < t1 && ts < tmax;
             if (isfinite(ts) && nxt >= 0) {
                 /* a hit next to the exit face: which cell it falls in is a tie */
@@ -443,7 +445,7 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
             double p[3], k;
             for (int a = 0; a < 3; ++a) p[a] = o[a] + ts * d[a];
             if (sphere_bounce(E, p, d, inside, &k)) inside = !inside;
-            if (E->ior > 0.0 && fabs(k) < 1e-4) R->degen = 1;  /* near the critical angle */
+            if (E->ior > 0.0 && fabs(k) < 1e-2) R->degen = 1;  /* near the critical angle */
             for (int a = 0; a < 3; ++a) o[a] = p[a];
             s_off += ts;
             t0 = 0.0;
