@@ -362,7 +362,7 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
         if (steps >= max_steps) { R->status = ORC_RAY_MAX_STEPS; break; }
         const double *x = S->pos + 3 * i;
         /* nearest front-facing bisector plane (Fig. 3) */
-        double t1 = HUGE_VAL, cos_exit = 1.0;
+        double t1 = HUGE_VAL, cos_exit = 1.0, len_exit = 1.0;
         int64_t nxt = -1;
         for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
             const int64_t j = S->adj[f];
@@ -377,7 +377,7 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
             }
             if (den > 0.0) {
                 const double t = num / den;
-                if (t < t1) { t1 = t; nxt = j; cos_exit = den / sqrt(nn); }
+                if (t < t1) { t1 = t; nxt = j; cos_exit = den / sqrt(nn); len_exit = sqrt(nn); }
             }
         }
         /* does the ray meet the sphere inside this cell? */
@@ -398,10 +398,14 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
             }
         }
         const double tend = hit ? ts : t1;
-        /* a crossing at grazing incidence: its point on the face moves by
-         * ~ (direction error) / cos along the face, so its gradient is
-         * ill-conditioned in any working precision */
-        if (!hit && nxt >= 0 && t1 < tmax && cos_exit < 1e-3) R->degen = 1;
+        /* a crossing at grazing incidence: a rounding of the direction
+         * (~1e-7 relative) or of the coordinates (~tau / 10) moves its point
+         * along the face by (1e-7 |t| + tau / 10) / cos; flagged when that
+         * exceeds 1e-3 of the distance between the two sites, where the
+         * crossing's position gradient is ill-conditioned at FP32 */
+        if (!hit && nxt >= 0 && t1 < tmax && tau > 0.0 &&
+            (1e-7 * fabs(t1) + 0.1 * tau) > 1e-3 * cos_exit * len_exit)
+            R->degen = 1;
         /* degeneracy test at the step's end point */
         {
             const double te = (hit || (nxt >= 0 && t1 < tmax)) ? tend : tmax;
