@@ -100,22 +100,35 @@ typedef struct rf_scene_desc {
 } rf_scene_desc;
 
 /*
- * Pinhole camera (the ray origins o and unit directions d of Alg. 1).
+ * Camera (the ray origins o and unit directions d of Alg. 1; the camera
+ * models and the rolling shutter are the non-linear cameras of the paper's
+ * ray-based effects figure, Fig. 2).
  *   c2w      row-major 3x4 [R | t]: camera-frame point x -> R x + t; the
  *            camera frame is OpenCV (+x right, +y down, +z forward); t is the
- *            centre (every ray's origin o).
+ *            centre.
  *   fx, fy, cx, cy  intrinsics in pixels; pixel (u,v) casts the ray through
- *            its centre (u+0.5, v+0.5), d = normalise(R ((u+.5-cx)/fx,
- *            (v+.5-cy)/fy, 1)).
+ *            its centre: x = (u+.5-cx)/fx, y = (v+.5-cy)/fy and
+ *            RF_CAM_PINHOLE:  d = normalise(R (x, y, 1));
+ *            RF_CAM_FISHEYE:  equidistant, th = sqrt(x^2+y^2) is the angle to
+ *                             the optical axis, d = R (x sin(th)/th,
+ *                             y sin(th)/th, cos(th)).
  *   width, height   image size; ray index = v * width + u.
  *   t_near, t_far   compositing interval along d, intersected with the scene
  *            box (t_far <= 0: no limit).
+ *   model    RF_CAM_PINHOLE or RF_CAM_FISHEYE.
+ *   shutter  rolling shutter: displacement of the centre over the frame;
+ *            row v's rays start at t + ((v+.5)/height - .5) * shutter
+ *            (all zero: global shutter, every ray starts at t).
  */
+enum { RF_CAM_PINHOLE = 0, RF_CAM_FISHEYE = 1 };
+
 typedef struct rf_camera {
     float c2w[12];
     float fx, fy, cx, cy;
     int32_t width, height;
     float t_near, t_far;
+    int32_t model;
+    float shutter[3];
 } rf_camera;
 
 /*
@@ -124,12 +137,27 @@ typedef struct rf_camera {
  *   max_steps  cap on cell steps per ray (<= 0: 65536); a capped ray gets
  *              RF_RAY_MAX_STEPS.
  *   flags      reserved, 0.
+ *   max_bounces, sphere, sphere_ior  optional analytic sphere met in the
+ *              same walk (reflection / refraction of Fig. 2): centre
+ *              sphere[0..2], radius sphere[3] > 0; sphere_ior = 0 for a
+ *              perfect mirror, > 0 for clear glass of that refractive index
+ *              (Snell refraction, total internal reflection).  In each cell
+ *              a hit before the exit face ends the segment there; the ray
+ *              bends at the hit point and walks on from the same cell with
+ *              t0 = 0, clipped to the scene box only.  A ray meets the
+ *              sphere at most max_bounces times, then passes through it.
+ *              max_bounces = 0: no sphere.  Depth is the path length along
+ *              the bent ray.  The sphere is fixed: it receives no gradient
+ *              and passes none to the sites.
  */
 typedef struct rf_render_opts {
     float eps;
     int32_t max_steps;
     uint32_t flags;
     int32_t reserved;
+    int32_t max_bounces;
+    float sphere[4];
+    float sphere_ior;
 } rf_render_opts;
 
 typedef struct rf_scene rf_scene;
@@ -347,6 +375,10 @@ RF_API rf_status rf_serve_destroy(rf_server *srv);
  *   - the first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress), so make that first call before any stream
  *     capture.
+ * Pinhole and fisheye cameras are supported; a rolling shutter (nonzero
+ * camera shutter) or a sphere (opts->max_bounces > 0) returns
+ * RF_ERR_INVALID_ARG: their per-ray start cells and bounces need the packed
+ * scene.
  */
 RF_API rf_status rf_render_fwd_noalloc(int64_t n_sites, int64_t n_edges, const float *pos,
                                        const int32_t *adj_off, const int32_t *adj_idx,

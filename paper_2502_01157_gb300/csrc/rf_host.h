@@ -44,7 +44,7 @@ rf_status cuda_fail(cudaError_t e, const char *what);
 
 SceneDev scene_dev(const rf_scene *s);
 rf_status check_camera(const rf_camera &c, int index);
-rf_status check_opts(const rf_render_opts *o, float *eps, int32_t *max_steps);
+rf_status check_opts(const rf_render_opts *o, float *eps, int32_t *max_steps, SphereFx *fx);
 
 // Start cells nn(o) of cams[0..n) (n <= kMaxCamsPerLaunch) into keys[0..n).
 rf_status launch_nearest_sites(const rf_scene *s, const rf_camera *cams, int n,

@@ -59,12 +59,20 @@ struct LaunchCams {
     int32_t cam0;                               // index of cam[0] in the start-cell table
 };
 
+// Optional analytic sphere of the walk (mirror: ior = 0; glass: ior > 0).
+struct SphereFx {
+    float cx, cy, cz, r;
+    float ior;
+    int32_t max_bounces;  // 0: no sphere
+};
+
 struct RenderParams {
     SceneDev s;
     LaunchCams lc;
     const unsigned long long *start_keys;  // [cam0 + c] low 32 bits: start cell
     float eps;
     int32_t max_steps;
+    SphereFx fx;
 };
 
 // ---------------------------------------------------------------------------
@@ -126,16 +134,44 @@ __device__ __forceinline__ PixelTask pixel_of_thread(const LaunchCams &lc) {
     return t;
 }
 
-// Pinhole ray through the centre of pixel (u, v).
+__device__ __forceinline__ bool has_shutter(const rf_camera &c) {
+    return c.shutter[0] != 0.f || c.shutter[1] != 0.f || c.shutter[2] != 0.f;
+}
+
+// Ray through the centre of pixel (u, v): pinhole, or equidistant fisheye
+// (the angle to the optical axis equals the normalised image radius); with a
+// rolling shutter the origin of row v moves by ((v + 1/2)/H - 1/2) shutter.
+// EXT = false compiles the pinhole, global-shutter case only (the launch has
+// no other camera); its arithmetic is the same as EXT's pinhole branch.
+template <bool EXT>
 __device__ __forceinline__ void camera_ray(const rf_camera &c, int u, int v, float3 &o, float3 &d) {
-    const float xc = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), c.cx), c.fx);
-    const float yc = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), c.cy), c.fy);
-    const float wx = __fmaf_rn(c.c2w[0], xc, __fmaf_rn(c.c2w[1], yc, c.c2w[2]));
-    const float wy = __fmaf_rn(c.c2w[4], xc, __fmaf_rn(c.c2w[5], yc, c.c2w[6]));
-    const float wz = __fmaf_rn(c.c2w[8], xc, __fmaf_rn(c.c2w[9], yc, c.c2w[10]));
+    float xc = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), c.cx), c.fx);
+    float yc = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), c.cy), c.fy);
+    float wx, wy, wz;
+    if (EXT && c.model == RF_CAM_FISHEYE) {
+        const float th = __fsqrt_rn(__fmaf_rn(xc, xc, __fmul_rn(yc, yc)));
+        float sn, cs;
+        sincospif(__fmul_rn(th, 0.318309886183790672f), &sn, &cs);  // th / pi: no wide range reduction
+        const float sc = th > 0.f ? __fdiv_rn(sn, th) : 1.f;
+        xc = __fmul_rn(xc, sc);
+        yc = __fmul_rn(yc, sc);
+        wx = __fmaf_rn(c.c2w[0], xc, __fmaf_rn(c.c2w[1], yc, __fmul_rn(c.c2w[2], cs)));
+        wy = __fmaf_rn(c.c2w[4], xc, __fmaf_rn(c.c2w[5], yc, __fmul_rn(c.c2w[6], cs)));
+        wz = __fmaf_rn(c.c2w[8], xc, __fmaf_rn(c.c2w[9], yc, __fmul_rn(c.c2w[10], cs)));
+    } else {
+        wx = __fmaf_rn(c.c2w[0], xc, __fmaf_rn(c.c2w[1], yc, c.c2w[2]));
+        wy = __fmaf_rn(c.c2w[4], xc, __fmaf_rn(c.c2w[5], yc, c.c2w[6]));
+        wz = __fmaf_rn(c.c2w[8], xc, __fmaf_rn(c.c2w[9], yc, c.c2w[10]));
+    }
     const float len = __fsqrt_rn(__fmaf_rn(wx, wx, __fmaf_rn(wy, wy, __fmul_rn(wz, wz))));
     d = make_float3(__fdiv_rn(wx, len), __fdiv_rn(wy, len), __fdiv_rn(wz, len));
     o = make_float3(c.c2w[3], c.c2w[7], c.c2w[11]);
+    if (EXT && has_shutter(c)) {
+        const float row = __fsub_rn(__fdiv_rn(__fadd_rn((float)v, 0.5f), (float)c.height), 0.5f);
+        o.x = __fmaf_rn(row, c.shutter[0], o.x);
+        o.y = __fmaf_rn(row, c.shutter[1], o.y);
+        o.z = __fmaf_rn(row, c.shutter[2], o.z);
+    }
 }
 
 // Clip the ray to [t_near, t_far] and the scene box (slab test).
@@ -321,23 +357,151 @@ struct Segment {
     float e;       // exp(-sigma delta)
     float pre[3];  // colour before the clamp
     int next;
+    bool hit;      // the segment ends on the sphere at ts (FX kernels)
 };
 
-template <typename AT, int DEG>
+// With FX, ts is the current ray's next sphere crossing (+inf: none): when it
+// falls in [t0, t1) and before t_max the segment ends there instead of at the
+// face.
+template <typename AT, int DEG, bool FX = false>
 __device__ __forceinline__ void cell_step(const SceneDev &s, int i, const CellHdr &cell,
                                           const float3 &o, const float3 &d, float t0, float tmin,
-                                          float tmax, const float *Y, Segment &g, float3 &oc) {
+                                          float tmax, const float *Y, Segment &g, float3 &oc,
+                                          float ts = 0.f) {
     oc = make_float3(__fsub_rn(o.x, cell.x), __fsub_rn(o.y, cell.y), __fsub_rn(o.z, cell.z));
     float nb, db;
     g.next = find_exit(s, cell, d, oc, nb, db);
     g.t1 = g.next >= 0 ? __fdiv_rn(nb, db) : __int_as_float(0x7f800000);
     g.a = t0 > tmin ? t0 : tmin;
-    g.b = g.t1 < tmax ? g.t1 : tmax;
+    float tend = g.t1;
+    g.hit = false;
+    if constexpr (FX) {
+        g.hit = ts >= t0 && ts < g.t1 && ts < tmax;
+        if (g.hit) tend = ts;
+    }
+    g.b = tend < tmax ? tend : tmax;
     const float w = __fsub_rn(g.b, g.a);
     g.delta = w > 0.f ? w : 0.f;
     g.sigma = to_f(ldg(reinterpret_cast<const AT *>(s.density) + i));
     g.e = expf(-__fmul_rn(g.sigma, g.delta));
     sh_colour<AT, DEG>(reinterpret_cast<const AT *>(s.sh), i, Y, g.pre, s.sh_v8 != 0);
+}
+
+// ---------------------------------------------------------------------------
+// Sphere bounces (reflection / refraction met in the walk, Fig. 2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dot3(const float3 &a, const float3 &b) {
+    return __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, __fmul_rn(a.z, b.z)));
+}
+
+// Parameter of the ray's next crossing of the sphere (the entry from
+// outside, the exit from inside), +inf if none lies ahead.  The
+// discriminant is r^2 - h^2 with h the distance of the centre from the ray
+// (no cancellation when the origin lies on the sphere after a bounce).
+__device__ __forceinline__ float sphere_next(const SphereFx &fx, const float3 &o, const float3 &d,
+                                             bool inside) {
+    const float3 oc = make_float3(__fsub_rn(o.x, fx.cx), __fsub_rn(o.y, fx.cy), __fsub_rn(o.z, fx.cz));
+    const float b = dot3(d, oc);
+    const float3 q = make_float3(__fmaf_rn(-b, d.x, oc.x), __fmaf_rn(-b, d.y, oc.y), __fmaf_rn(-b, d.z, oc.z));
+    const float disc = __fsub_rn(__fmul_rn(fx.r, fx.r), dot3(q, q));
+    if (!(disc >= 0.f)) return __int_as_float(0x7f800000);
+    const float w = __fsqrt_rn(disc);
+    const float t = inside ? __fadd_rn(-b, w) : __fsub_rn(-b, w);
+    return t > 0.f ? t : __int_as_float(0x7f800000);
+}
+
+// Bend the ray at the hit point p: mirror reflection, or Snell refraction
+// with relative index 1/n entering and n leaving (total internal reflection
+// when no refracted ray exists).  Updates d (unit) and the inside flag.
+__device__ __forceinline__ void sphere_bend(const SphereFx &fx, const float3 &p, float3 &d, bool &inside) {
+    const float ir = __fdiv_rn(1.f, fx.r);
+    const float3 n = make_float3(__fmul_rn(__fsub_rn(p.x, fx.cx), ir), __fmul_rn(__fsub_rn(p.y, fx.cy), ir),
+                                 __fmul_rn(__fsub_rn(p.z, fx.cz), ir));
+    const float dn = dot3(d, n);
+    bool crossed = false;
+    float3 r;
+    if (fx.ior > 0.f) {
+        const float sg = inside ? -1.f : 1.f;              // normal on the incoming side: sg n
+        const float eta = inside ? fx.ior : __fdiv_rn(1.f, fx.ior);
+        const float ci = __fmul_rn(-dn, sg);
+        const float k = __fsub_rn(1.f, __fmul_rn(__fmul_rn(eta, eta), __fsub_rn(1.f, __fmul_rn(ci, ci))));
+        if (k >= 0.f) {
+            const float f = __fmul_rn(__fsub_rn(__fmul_rn(eta, ci), __fsqrt_rn(k)), sg);
+            r = make_float3(__fmaf_rn(eta, d.x, __fmul_rn(f, n.x)), __fmaf_rn(eta, d.y, __fmul_rn(f, n.y)),
+                            __fmaf_rn(eta, d.z, __fmul_rn(f, n.z)));
+            crossed = true;
+        }
+    }
+    if (!crossed) {
+        const float m = __fmul_rn(-2.f, dn);
+        r = make_float3(__fmaf_rn(m, n.x, d.x), __fmaf_rn(m, n.y, d.y), __fmaf_rn(m, n.z, d.z));
+    } else {
+        inside = !inside;
+    }
+    const float len = __fsqrt_rn(dot3(r, r));
+    d = make_float3(__fdiv_rn(r.x, len), __fdiv_rn(r.y, len), __fdiv_rn(r.z, len));
+}
+
+// State of a ray that may bounce off the sphere.
+struct FxRay {
+    float ts;      // next sphere crossing on the current leg (+inf: none)
+    float soff;    // path length before the current leg's origin
+    int bounces;
+    bool inside;
+};
+
+__device__ __forceinline__ void fx_begin(const SphereFx &fx, const float3 &o, const float3 &d, FxRay &f) {
+    const float3 oc = make_float3(__fsub_rn(o.x, fx.cx), __fsub_rn(o.y, fx.cy), __fsub_rn(o.z, fx.cz));
+    f.inside = dot3(oc, oc) < __fmul_rn(fx.r, fx.r);
+    f.soff = 0.f;
+    f.bounces = 0;
+    f.ts = fx.max_bounces > 0 ? sphere_next(fx, o, d, f.inside) : __int_as_float(0x7f800000);
+}
+
+// After a segment that ended on the sphere: move the origin to the hit
+// point, bend the direction, clip the new leg to the scene box.  Returns
+// false when the new leg has no part inside the box.
+__device__ __forceinline__ bool fx_bounce(const SphereFx &fx, const SceneDev &s, FxRay &f, float3 &o,
+                                          float3 &d, float &tmin, float &tmax) {
+    const float3 p = make_float3(__fmaf_rn(f.ts, d.x, o.x), __fmaf_rn(f.ts, d.y, o.y), __fmaf_rn(f.ts, d.z, o.z));
+    sphere_bend(fx, p, d, f.inside);
+    o = p;
+    f.soff = __fadd_rn(f.soff, f.ts);
+    ++f.bounces;
+    if (!ray_interval(o, d, s, 0.f, 0.f, tmin, tmax)) return false;
+    f.ts = f.bounces < fx.max_bounces ? sphere_next(fx, o, d, f.inside) : __int_as_float(0x7f800000);
+    return true;
+}
+
+// Start cell of a rolling-shutter row: the cell containing the row's origin
+// q, reached by walking the segment from the centre c (in cell i) to q
+// through the foam with the same exit search as the ray walk.
+__device__ __forceinline__ int locate_from(const SceneDev &s, int i, const float3 &c, const float3 &q,
+                                           int max_steps) {
+    const float3 v = make_float3(__fsub_rn(q.x, c.x), __fsub_rn(q.y, c.y), __fsub_rn(q.z, c.z));
+    const float L = __fsqrt_rn(dot3(v, v));
+    if (!(L > 0.f)) return i;
+    const float3 d = make_float3(__fdiv_rn(v.x, L), __fdiv_rn(v.y, L), __fdiv_rn(v.z, L));
+    for (int k = 0; k < max_steps; ++k) {
+        const CellHdr cell = load_cell(s, i);
+        const float3 oc = make_float3(__fsub_rn(c.x, cell.x), __fsub_rn(c.y, cell.y), __fsub_rn(c.z, cell.z));
+        float nb, db;
+        const int nx = find_exit(s, cell, d, oc, nb, db);
+        if (nx < 0 || !(__fdiv_rn(nb, db) < L)) break;
+        i = nx;
+    }
+    return i;
+}
+
+// Start cell of a ray: nn(camera centre) from the per-camera table, moved to
+// the row's origin for a rolling shutter.
+template <bool EXT>
+__device__ __forceinline__ int start_cell(const RenderParams &p, int cam, const float3 &o) {
+    int i = (int)(p.start_keys[p.lc.cam0 + cam] & 0xffffffffull);
+    const rf_camera &c = p.lc.cam[cam];
+    if (EXT && has_shutter(c))
+        i = locate_from(p.s, i, make_float3(c.c2w[3], c.c2w[7], c.c2w[11]), o, p.max_steps);
+    return i;
 }
 
 // ---------------------------------------------------------------------------

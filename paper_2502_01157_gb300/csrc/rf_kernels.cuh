@@ -1,0 +1,528 @@
+// rf_kernels.cuh -- forward, backward and trace kernels of the Radiant Foam
+// renderer (arXiv 2502.01157) for sm_103a, templated on the attribute type,
+// the SH degree, the output mode and FX.  FX kernels handle the ray-based
+// effects of Fig. 2 -- fisheye cameras, rolling shutters and an analytic
+// sphere met in the walk -- and the others only pinhole, global-shutter
+// cameras without a sphere, so that the common path keeps its registers.
+// rf_render.cu instantiates the plain kernels and rf_effects.cu the FX ones,
+// so the two halves compile in parallel.
+//
+// One thread per ray.  A block renders a 16x8 pixel tile of one camera; each
+// warp owns an 8x4 patch, so the rays of a warp enter mostly the same cells
+// and their face loads hit the same L1 lines.  Tiles of all cameras of a call
+// form one grid (multi-camera batches are one launch).
+#pragma once
+
+#include "rf_host.h"
+
+namespace rf {
+
+struct FwdOut {
+    float *rgb;
+    float *trans;
+    float *depth;
+    int32_t *steps;
+    uint8_t *status;
+    int32_t *trace;     // [R][max_trace] or null
+    int32_t max_trace;
+    float *quantile;    // [R] (mode kQuant)
+    float *qaux;        // [R][5]: D, Q, W, Z1, Z2 (mode kQuant)
+};
+
+enum { kPlain = 0, kTrace = 1, kQuant = 2 };
+
+// Forward: Alg. 1 per ray with Eq. (3)-(4) compositing; in mode kQuant the
+// same walk also accumulates the quantile loss of Eq. (6).  With FX the walk
+// meets the sphere of p.fx (if max_bounces > 0): a hit ends the segment, bends
+// the ray and the walk carries on from the same cell (depth then measures the
+// bent path).
+template <typename AT, int DEG, int MODE, bool FX>
+__global__ void __launch_bounds__(kBlock) fwd_kernel(const RenderParams p, const FwdOut out) {
+    constexpr bool TRACE = MODE == kTrace;
+    constexpr bool QUANT = MODE == kQuant;
+    const PixelTask px = pixel_of_thread(p.lc);
+    if (!px.valid) return;
+    const rf_camera &cam = p.lc.cam[px.cam];
+    float3 o, d;
+    camera_ray<FX>(cam, px.u, px.v, o, d);
+    const int64_t r = p.lc.ray_begin[px.cam] + (int64_t)px.v * cam.width + px.u;
+
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, T = 1.f;
+    float qP = 0.f, qQ = 0.f, qW = 0.f, qZ1 = 0.f, qZ2 = 0.f;  // quantile-loss sums
+    int steps = 0;
+    uint8_t st = RF_RAY_OK;
+    float tmin, tmax;
+    if (ray_interval(o, d, p.s, cam.t_near, cam.t_far, tmin, tmax)) {
+        float Y[16];
+        sh_basis<DEG>(d, Y);
+        int i = start_cell<FX>(p, px.cam, o);
+        float t0 = 0.f;
+        FxRay f;
+        if constexpr (FX) fx_begin(p.fx, o, d, f);
+        while (T > p.eps) {
+            if (steps >= p.max_steps) {
+                st = RF_RAY_MAX_STEPS;
+                break;
+            }
+            const CellHdr cell = load_cell(p.s, i);
+            Segment g;
+            float3 oc;
+            cell_step<AT, DEG, FX>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc, FX ? f.ts : 0.f);
+            if (TRACE && steps < out.max_trace) out.trace[r * out.max_trace + steps] = i;
+            const float alpha = __fsub_rn(1.f, g.e);
+            const float w = __fmul_rn(T, alpha);
+            C0 = __fmaf_rn(w, fmaxf(g.pre[0], 0.f), C0);
+            C1 = __fmaf_rn(w, fmaxf(g.pre[1], 0.f), C1);
+            C2 = __fmaf_rn(w, fmaxf(g.pre[2], 0.f), C2);
+            float z = __fmul_rn(0.5f, __fadd_rn(g.a, g.b));
+            if constexpr (FX) z = __fadd_rn(f.soff, z);
+            D = __fmaf_rn(w, z, D);
+            if (QUANT && g.delta > 0.f) {
+                const QuantSeg q = quant_seg(g.sigma, g.delta, g.e);
+                qQ += qW * g.delta + T * q.f1d;                            // int W
+                qP += qW * (qW * g.delta + 2.f * T * q.f1d) + T * T * q.f2d;  // int W^2
+                qZ1 += T * ((1.f - 2.f * T) * q.A + 2.f * T * q.C);
+                qZ2 += T * q.A;
+                qW += T * q.alpha;                                         // weight so far
+            }
+            T = __fmul_rn(T, g.e);
+            ++steps;
+            if (FX && g.hit) {
+                if (!fx_bounce(p.fx, p.s, f, o, d, tmin, tmax)) break;
+                sh_basis<DEG>(d, Y);
+                t0 = 0.f;
+                continue;  // the new leg starts in the same cell
+            }
+            if (g.next < 0 || !(g.t1 < tmax)) break;
+            t0 = g.t1 > t0 ? g.t1 : t0;
+            i = g.next;
+        }
+    }
+    if (QUANT) {
+        const float qD = qW * qQ - qP;  // int W (W_tot - W) dt = int (1 - T)(T - T_f) dt
+        out.quantile[r] = qW > 0.f ? 2.f * qD / (qW * qW) : 0.f;
+        float *a = out.qaux + 5 * r;
+        a[0] = qD;
+        a[1] = qQ;
+        a[2] = qW;
+        a[3] = qZ1;
+        a[4] = qZ2;
+    }
+    if (TRACE) {
+        for (int k = steps; k < out.max_trace; ++k) out.trace[r * out.max_trace + k] = -1;
+        out.steps[r] = steps;
+        return;
+    }
+    out.rgb[3 * r + 0] = C0;
+    out.rgb[3 * r + 1] = C1;
+    out.rgb[3 * r + 2] = C2;
+    out.trans[r] = T;
+    out.depth[r] = D;
+    if (out.steps) out.steps[r] = steps;
+    if (out.status) out.status[r] = st;
+}
+
+struct BwdIO {
+    const float *rgb, *trans, *depth;
+    const float *d_rgb, *d_trans, *d_depth;
+    float *g_density, *g_sh, *g_pos;
+    int32_t sh_vec;  // g_sh rows may use 16-byte atomics
+    const float *qaux, *d_quantile;
+};
+
+template <int DEG>
+__device__ __forceinline__ void scatter_sh(float *__restrict__ g_sh, int i, const float *cb,
+                                           const float *Y, bool vec) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int NV = 3 * K;
+    float *row = g_sh + (size_t)i * NV;
+    if constexpr (NV % 4 == 0) {
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < NV / 4; ++q) {
+                float4 v;
+                v.x = cb[(4 * q + 0) % 3] * Y[(4 * q + 0) / 3];
+                v.y = cb[(4 * q + 1) % 3] * Y[(4 * q + 1) / 3];
+                v.z = cb[(4 * q + 2) % 3] * Y[(4 * q + 2) / 3];
+                v.w = cb[(4 * q + 3) % 3] * Y[(4 * q + 3) / 3];
+                atomicAdd(reinterpret_cast<float4 *>(row) + q, v);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NV; ++g)
+        if (cb[g % 3] != 0.f) atomicAdd(row + g, cb[g % 3] * Y[g / 3]);
+}
+
+// Backward: the walk of the forward is repeated with identical arithmetic;
+// per segment the adjoints follow from the stored final colour, transmittance
+// and depth (C_rest = C_final - C_incl).
+//
+// Scatter.  Neighbouring rays of a warp mostly walk the same cells (a warp of
+// an 8x4 patch meets ~5 distinct cells per iteration at 1920x1080 and reuses
+// each ~25 times over its walk), so per-lane atomics would hit the same
+// addresses many times.  Each iteration the lanes stage their contributions
+// (SH row, density, the two site positions of the crossing that entered the
+// cell) in shared memory; lanes with the same (previous cell, cell) pair are
+// summed column-wise and the sum is added with one coalesced atomic per
+// value.  A warp whose lanes are spread over many cells scatters per lane.
+constexpr int kMaxGroups = 12;
+
+template <typename AT, int DEG, bool QUANT, bool FX>
+__global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, const BwdIO io) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int NV = 3 * K;       // SH gradient row
+    constexpr int V = NV + 7;       // + density, position of the cell, position of the previous cell
+    constexpr int VP = (V + 3) / 4 * 4;
+    // row stride: a multiple of 4 floats (16-byte row stores) whose quarter is
+    // odd, so the 8 lanes of a 128-bit store phase hit 8 different bank quads;
+    // a column read (one row, consecutive columns) is conflict-free for any stride
+    constexpr int SP = ((VP / 4) % 2 == 1) ? VP : VP + 4;
+    // 32 lane rows + one zero row that pads the 4-member unrolled sums
+    __shared__ __align__(16) float stage_all[kBlock / 32][33 * SP];
+    const int lane = threadIdx.x & 31;
+    float *stage = stage_all[threadIdx.x >> 5];
+    const unsigned full = 0xffffffffu;
+    for (int c = lane; c < SP; c += 32) stage[32 * SP + c] = 0.f;
+    __syncwarp();
+
+    // per-lane set-up; no early return: every lane takes part in the
+    // warp-wide scatter until the whole warp is done
+    const PixelTask px = pixel_of_thread(p.lc);
+    bool live = px.valid;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+    float tmin = 0.f, tmax = 0.f;
+    int64_t r = 0;
+    if (live) {
+        const rf_camera &cam = p.lc.cam[px.cam];
+        camera_ray<FX>(cam, px.u, px.v, o, d);
+        r = p.lc.ray_begin[px.cam] + (int64_t)px.v * cam.width + px.u;
+        live = ray_interval(o, d, p.s, cam.t_near, cam.t_far, tmin, tmax);
+    }
+    float gC[3] = {0.f, 0.f, 0.f}, gT = 0.f, gD = 0.f, Cf[3] = {0.f, 0.f, 0.f}, Tf = 0.f, Df = 0.f;
+    if (live) {
+        gC[0] = io.d_rgb[3 * r];
+        gC[1] = io.d_rgb[3 * r + 1];
+        gC[2] = io.d_rgb[3 * r + 2];
+        gT = io.d_trans ? io.d_trans[r] : 0.f;
+        gD = io.d_depth ? io.d_depth[r] : 0.f;
+        live = !(gC[0] == 0.f && gC[1] == 0.f && gC[2] == 0.f && gT == 0.f && gD == 0.f);
+        if (QUANT) live = live || io.d_quantile[r] != 0.f;
+        Cf[0] = io.rgb[3 * r];
+        Cf[1] = io.rgb[3 * r + 1];
+        Cf[2] = io.rgb[3 * r + 2];
+        Tf = io.trans[r];
+        Df = io.depth ? io.depth[r] : 0.f;
+    }
+    // quantile loss L = 2 (P - T_f Q) / W^2: per-segment adjoints from the
+    // forward's sums; suffix sums of Z1 + T_f Z2 carry the dependence of the
+    // later segments on this segment's transmittance factor
+    float gQ = 0.f, qk2 = 0.f, qdTf = 0.f, qZ1 = 0.f, qZ2 = 0.f, qW = 0.f;
+    if (QUANT && live) {
+        gQ = io.d_quantile[r];
+        const float *a = io.qaux + 5 * r;
+        qW = a[2];
+        if (gQ != 0.f && qW > 0.f) {
+            qk2 = 2.f / (qW * qW);
+            qdTf = -qk2 * a[1] + 2.f * qk2 * a[0] / qW;  // dL/dT_f at fixed P, Q (a[0] = P - T_f Q)
+            qZ1 = a[3];
+            qZ2 = a[4];
+        } else {
+            gQ = 0.f;
+        }
+    }
+    float qWn = 0.f;  // weight before the current segment
+    float Y[16];
+    sh_basis<DEG>(d, Y);
+    int i = live ? start_cell<FX>(p, px.cam, o) : 0;
+    FxRay f;
+    if constexpr (FX) fx_begin(p.fx, o, d, f);
+    float t0 = 0.f, T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    int steps = 0;
+    // the crossing that entered the current cell: (pa -> i) at pt; its adjoint
+    // padj is complete once the current segment's t0 adjoint is known
+    bool pend = false, pend_defines = false;
+    int pa = -1;
+    float3 pxa = make_float3(0.f, 0.f, 0.f), poca = pxa;
+    float pt = 0.f, padj = 0.f;
+    // the crossing that set the current t0 (t0 <- max(t0, t1))
+    int da = -1, db = -1;
+    float dt = 0.f;
+
+    while (__any_sync(full, live)) {
+        // stop tests of Alg. 1 (before the step); a crossing still pending
+        // (T fell to eps right after it) is scattered by this lane alone
+        if (live && (!(T > p.eps) || steps >= p.max_steps)) {
+            live = false;
+            if (pend && padj != 0.f && io.g_pos) {
+                const CellHdr cb = load_cell(p.s, i);
+                const float3 xb = make_float3(cb.x, cb.y, cb.z);
+                const float nx = xb.x - pxa.x, ny = xb.y - pxa.y, nz = xb.z - pxa.z;
+                const float s_ = padj / (nx * d.x + ny * d.y + nz * d.z);
+                const float qx = poca.x + pt * d.x, qy = poca.y + pt * d.y, qz = poca.z + pt * d.z;
+                atomicAdd(io.g_pos + 3 * (int64_t)pa + 0, s_ * qx);
+                atomicAdd(io.g_pos + 3 * (int64_t)pa + 1, s_ * qy);
+                atomicAdd(io.g_pos + 3 * (int64_t)pa + 2, s_ * qz);
+                atomicAdd(io.g_pos + 3 * (int64_t)i + 0, s_ * (nx - qx));
+                atomicAdd(io.g_pos + 3 * (int64_t)i + 1, s_ * (ny - qy));
+                atomicAdd(io.g_pos + 3 * (int64_t)i + 2, s_ * (nz - qz));
+            }
+        }
+        float sig_bar = 0.f, cb[3] = {0.f, 0.f, 0.f};
+        float gpos_i[3] = {0.f, 0.f, 0.f}, gpos_a[3] = {0.f, 0.f, 0.f};
+        int key_prev = -1;
+        Segment g;
+        CellHdr cell;
+        float3 oc = make_float3(0.f, 0.f, 0.f);
+        if (live) {
+            cell = load_cell(p.s, i);
+            cell_step<AT, DEG, FX>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc, FX ? f.ts : 0.f);
+            const float alpha = __fsub_rn(1.f, g.e);
+            const float w = __fmul_rn(T, alpha);
+            const float c[3] = {fmaxf(g.pre[0], 0.f), fmaxf(g.pre[1], 0.f), fmaxf(g.pre[2], 0.f)};
+            float z = __fmul_rn(0.5f, __fadd_rn(g.a, g.b));
+            if constexpr (FX) z = __fadd_rn(f.soff, z);
+            C0 = __fmaf_rn(w, c[0], C0);
+            C1 = __fmaf_rn(w, c[1], C1);
+            C2 = __fmaf_rn(w, c[2], C2);
+            D = __fmaf_rn(w, z, D);
+            const float Tn = __fmul_rn(T, g.e);
+            // dL/dsigma_n = delta_n * B, dL/ddelta_n = sigma_n * B with
+            // B = g_C.(T_{n+1} c_n - C_rest) - g_T T_final + g_D (T_{n+1} z_n - D_rest)
+            const float B = gC[0] * (Tn * c[0] - (Cf[0] - C0)) + gC[1] * (Tn * c[1] - (Cf[1] - C1)) +
+                            gC[2] * (Tn * c[2] - (Cf[2] - C2)) - gT * Tf + gD * (Tn * z - (Df - D));
+            float qsig = 0.f, qdel = 0.f;
+            if (QUANT && gQ != 0.f) {
+                float dP_ds = 0.f, dP_dd = 0.f, dQ_ds = 0.f, dQ_dd = 0.f;
+                if (g.delta > 0.f) {
+                    const QuantSeg q = quant_seg(g.sigma, g.delta, g.e);
+                    qZ1 -= T * ((1.f - 2.f * T) * q.A + 2.f * T * q.C);  // now the suffix over later segments
+                    qZ2 -= T * q.A;
+                    dP_ds = T * (qWn * q.dA_ds + T * q.dC_ds);
+                    dP_dd = T * g.e * (qWn + T * q.alpha);
+                    dQ_ds = -T * q.dA_ds;
+                    dQ_dd = qWn + T * q.alpha;
+                    qWn += T * q.alpha;
+                }
+                const float later = qk2 * (qZ1 + Tf * qZ2) + qdTf * Tf;
+                qsig = gQ * (qk2 * (dP_ds - Tf * dQ_ds) - g.delta * later);
+                qdel = gQ * (qk2 * (dP_dd - Tf * dQ_dd) - g.sigma * later);
+            }
+            sig_bar = io.g_density ? g.delta * B + qsig : 0.f;
+            if (io.g_sh) {
+                cb[0] = g.pre[0] > 0.f ? gC[0] * w : 0.f;
+                cb[1] = g.pre[1] > 0.f ? gC[1] * w : 0.f;
+                cb[2] = g.pre[2] > 0.f ? gC[2] * w : 0.f;
+            }
+            // segment bounds: delta = max(b - a, 0), z = (a + b)/2,
+            // a = max(t0, t_min), b = min(t1, t_max)
+            const float dbar = g.sigma * B + qdel;
+            float abar = 0.5f * gD * w, bbar = abar;
+            if (g.b > g.a) {
+                bbar += dbar;
+                abar -= dbar;
+            }
+            const float t1bar = g.t1 < tmax ? bbar : 0.f;
+            const float t0bar = t0 > tmin ? abar : 0.f;
+            if (pend) {
+                if (pend_defines) {
+                    padj += t0bar;
+                } else if (da >= 0 && t0bar != 0.f && io.g_pos) {
+                    // t0 was set by an earlier crossing (floating-point tie)
+                    const CellHdr ca = load_cell(p.s, da), cbh = load_cell(p.s, db);
+                    const float nx = cbh.x - ca.x, ny = cbh.y - ca.y, nz = cbh.z - ca.z;
+                    const float s_ = t0bar / (nx * d.x + ny * d.y + nz * d.z);
+                    const float qx = (o.x - ca.x) + dt * d.x, qy = (o.y - ca.y) + dt * d.y,
+                                qz = (o.z - ca.z) + dt * d.z;
+                    atomicAdd(io.g_pos + 3 * (int64_t)da + 0, s_ * qx);
+                    atomicAdd(io.g_pos + 3 * (int64_t)da + 1, s_ * qy);
+                    atomicAdd(io.g_pos + 3 * (int64_t)da + 2, s_ * qz);
+                    atomicAdd(io.g_pos + 3 * (int64_t)db + 0, s_ * (nx - qx));
+                    atomicAdd(io.g_pos + 3 * (int64_t)db + 1, s_ * (ny - qy));
+                    atomicAdd(io.g_pos + 3 * (int64_t)db + 2, s_ * (nz - qz));
+                }
+                // crossing (pa -> i) at pt: dt/dp_i = (p_i - x)/den, dt/dp_a = (x - p_a)/den,
+                // x = o + pt d, den = (p_i - p_a).d
+                if (padj != 0.f && io.g_pos) {
+                    const float nx = cell.x - pxa.x, ny = cell.y - pxa.y, nz = cell.z - pxa.z;
+                    const float s_ = padj / (nx * d.x + ny * d.y + nz * d.z);
+                    const float qx = poca.x + pt * d.x, qy = poca.y + pt * d.y, qz = poca.z + pt * d.z;
+                    gpos_a[0] = s_ * qx;
+                    gpos_a[1] = s_ * qy;
+                    gpos_a[2] = s_ * qz;
+                    gpos_i[0] = s_ * (nx - qx);
+                    gpos_i[1] = s_ * (ny - qy);
+                    gpos_i[2] = s_ * (nz - qz);
+                }
+                key_prev = pa;
+            }
+            // this step's exit becomes the pending crossing; a segment that
+            // ends on the (fixed) sphere has none, and the next leg's t0 = 0
+            // is set by no crossing
+            pend = g.next >= 0 && !(FX && g.hit);
+            if (FX && g.hit) da = -1;
+            pa = i;
+            pxa = make_float3(cell.x, cell.y, cell.z);
+            poca = oc;
+            pt = g.t1;
+            padj = t1bar;
+            pend_defines = g.t1 >= t0;
+            if (pend && pend_defines) {
+                da = i;
+                db = g.next;
+                dt = g.t1;
+            }
+            T = Tn;
+            ++steps;
+        }
+
+        // ---- warp-wide scatter of this iteration's contributions ----
+        const unsigned long long key =
+            live ? (((unsigned long long)(uint32_t)key_prev << 32) | (uint32_t)i) : ~0ull;
+        const unsigned peers = __match_any_sync(full, key);
+        // lanes that share their (previous cell, cell) with another lane are
+        // summed through shared memory; a lane alone scatters by itself
+        const bool shared_row = live && __popc(peers) > 1;
+        const bool lead = shared_row && lane == __ffs(peers) - 1;
+        unsigned leaders = __ballot_sync(full, lead);
+        const bool grouped = __popc(leaders) <= kMaxGroups;
+        if (live && (!shared_row || !grouped)) {
+            if (io.g_sh && (cb[0] != 0.f || cb[1] != 0.f || cb[2] != 0.f)) scatter_sh<DEG>(io.g_sh, i, cb, Y, io.sh_vec);
+            if (sig_bar != 0.f) atomicAdd(io.g_density + i, sig_bar);
+            if (key_prev >= 0 && io.g_pos) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (gpos_i[a] != 0.f) atomicAdd(io.g_pos + 3 * (int64_t)i + a, gpos_i[a]);
+                    if (gpos_a[a] != 0.f) atomicAdd(io.g_pos + 3 * (int64_t)key_prev + a, gpos_a[a]);
+                }
+            }
+        }
+        if (grouped && leaders) {
+            if (shared_row) {
+                // this lane's row: SH gradient, density, position of the cell,
+                // position of the previous cell, zero padding
+                float4 *row = reinterpret_cast<float4 *>(stage + lane * SP);
+#pragma unroll
+                for (int q4 = 0; q4 < VP / 4; ++q4) {
+                    float v[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c = 4 * q4 + e;
+                        v[e] = c < NV ? cb[c % 3] * Y[c / 3]
+                             : c == NV ? sig_bar
+                             : c < NV + 4 ? gpos_i[(c - NV - 1) % 3]
+                             : c < NV + 7 ? gpos_a[(c - NV - 4) % 3] : 0.f;
+                    }
+                    row[q4] = make_float4(v[0], v[1], v[2], v[3]);
+                }
+            }
+            __syncwarp();
+            const int c0 = lane, c1 = lane + 32;  // the two value columns this lane sums
+            while (leaders) {
+                const int L = __ffs(leaders) - 1;
+                leaders &= leaders - 1;
+                const unsigned m = __shfl_sync(full, peers, L);
+                const int cell_i = __shfl_sync(full, i, L);
+                const int cell_a = __shfl_sync(full, key_prev, L);
+                float s0 = 0.f, s1 = 0.f;
+                if (c0 < V) {  // a lane only reads the columns that exist (V may be < 32)
+                    // four members per pass with independent loads; an absent
+                    // member reads the zero row 32
+                    for (unsigned mm = m; mm;) {
+                        const int k0 = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const int k1 = mm ? __ffs(mm) - 1 : 32;
+                        mm &= mm - 1;
+                        const int k2 = mm ? __ffs(mm) - 1 : 32;
+                        mm &= mm - 1;
+                        const int k3 = mm ? __ffs(mm) - 1 : 32;
+                        mm &= mm - 1;
+                        s0 += (stage[k0 * SP + c0] + stage[k1 * SP + c0]) +
+                              (stage[k2 * SP + c0] + stage[k3 * SP + c0]);
+                        if (c1 < V)
+                            s1 += (stage[k0 * SP + c1] + stage[k1 * SP + c1]) +
+                                  (stage[k2 * SP + c1] + stage[k3 * SP + c1]);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int col = h ? c1 : c0;
+                    const float sum = h ? s1 : s0;
+                    if (col < V && sum != 0.f) {
+                        if (col < NV) atomicAdd(io.g_sh + (size_t)cell_i * NV + col, sum);
+                        else if (col == NV) atomicAdd(io.g_density + cell_i, sum);
+                        else if (col < NV + 4) atomicAdd(io.g_pos + 3 * (int64_t)cell_i + (col - NV - 1), sum);
+                        else if (cell_a >= 0) atomicAdd(io.g_pos + 3 * (int64_t)cell_a + (col - NV - 4), sum);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+
+        if (live) {
+            if (FX && g.hit) {
+                if (fx_bounce(p.fx, p.s, f, o, d, tmin, tmax)) {
+                    sh_basis<DEG>(d, Y);
+                    t0 = 0.f;  // the new leg starts in the same cell
+                } else {
+                    live = false;
+                }
+            } else if (g.next < 0 || !(g.t1 < tmax)) {
+                live = false;  // nothing pending: the exit lies at or beyond t_max
+            } else {
+                t0 = g.t1 > t0 ? g.t1 : t0;
+                i = g.next;
+            }
+        }
+    }
+}
+
+
+template <typename F>
+static void dispatch(int dtype, int deg, F &&f) {
+    auto by_deg = [&](auto tag) {
+        using AT = decltype(tag);
+        switch (deg) {
+            case 0: f.template operator()<AT, 0>(); break;
+            case 1: f.template operator()<AT, 1>(); break;
+            case 2: f.template operator()<AT, 2>(); break;
+            default: f.template operator()<AT, 3>(); break;
+        }
+    };
+    if (dtype == RF_BF16) by_deg(__nv_bfloat16());
+    else if (dtype == RF_F16) by_deg(__half());
+    else by_deg(float());
+}
+
+// Launch the forward (mode kPlain / kTrace / kQuant) or the backward over
+// `tiles` blocks for the scene's attribute type and SH degree.
+template <bool FX>
+void launch_fwd_any(int dtype, int deg, int mode, int64_t tiles, const RenderParams &p, const FwdOut &o,
+                    cudaStream_t st) {
+    dispatch(dtype, deg, [&]<typename AT, int DEG>() {
+        if (mode == kTrace) fwd_kernel<AT, DEG, kTrace, FX><<<(unsigned)tiles, kBlock, 0, st>>>(p, o);
+        else if (mode == kQuant) fwd_kernel<AT, DEG, kQuant, FX><<<(unsigned)tiles, kBlock, 0, st>>>(p, o);
+        else fwd_kernel<AT, DEG, kPlain, FX><<<(unsigned)tiles, kBlock, 0, st>>>(p, o);
+    });
+}
+
+template <bool FX>
+void launch_bwd_any(int dtype, int deg, bool quant, int64_t tiles, const RenderParams &p, const BwdIO &io,
+                    cudaStream_t st) {
+    dispatch(dtype, deg, [&]<typename AT, int DEG>() {
+        if (quant) bwd_kernel<AT, DEG, true, FX><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
+        else bwd_kernel<AT, DEG, false, FX><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
+    });
+}
+
+extern template void launch_fwd_any<false>(int, int, int, int64_t, const RenderParams &, const FwdOut &,
+                                           cudaStream_t);
+extern template void launch_fwd_any<true>(int, int, int, int64_t, const RenderParams &, const FwdOut &,
+                                          cudaStream_t);
+extern template void launch_bwd_any<false>(int, int, bool, int64_t, const RenderParams &, const BwdIO &,
+                                           cudaStream_t);
+extern template void launch_bwd_any<true>(int, int, bool, int64_t, const RenderParams &, const BwdIO &,
+                                          cudaStream_t);
+
+}  // namespace rf

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kBlock) raw_fwd_kernel(const RawParams p, floa
     if (!px.valid) return;
     const rf_camera &cam = p.lc.cam[px.cam];
     float3 o, d;
-    camera_ray(cam, px.u, px.v, o, d);
+    camera_ray<true>(cam, px.u, px.v, o, d);
     const int64_t r = p.lc.ray_begin[px.cam] + (int64_t)px.v * cam.width + px.u;
     SceneDev box;
     for (int a = 0; a < 3; ++a) {
@@ -220,10 +220,13 @@ RF_API rf_status rf_render_fwd_noalloc(int64_t n_sites, int64_t n_edges, const f
     for (int c = 0; c < n_cams; ++c) {
         rf_status rc = check_camera(cams[c], c);
         if (rc != RF_OK) return rc;
+        if (cams[c].shutter[0] != 0.f || cams[c].shutter[1] != 0.f || cams[c].shutter[2] != 0.f)
+            return fail(RF_ERR_INVALID_ARG, "rf_render_fwd_noalloc: camera %d has a rolling shutter, "
+                        "which needs a packed scene (rf_render_fwd)", c);
     }
     float eps;
     int32_t max_steps;
-    rf_status rc = check_opts(opts, &eps, &max_steps);
+    rf_status rc = check_opts(opts, &eps, &max_steps, nullptr);
     if (rc != RF_OK) return rc;
     unsigned long long *keys = nullptr;
     rc = keys_address(&keys);

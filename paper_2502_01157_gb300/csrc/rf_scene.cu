@@ -47,20 +47,31 @@ rf_status check_camera(const rf_camera &c, int index) {
     bool ok = c.width > 0 && c.height > 0 && (int64_t)c.width * c.height < (1ll << 31) &&
               std::isfinite(c.fx) && std::isfinite(c.fy) && c.fx != 0.f && c.fy != 0.f &&
               std::isfinite(c.cx) && std::isfinite(c.cy) && std::isfinite(c.t_near) &&
-              !std::isnan(c.t_far);
+              !std::isnan(c.t_far) && (c.model == RF_CAM_PINHOLE || c.model == RF_CAM_FISHEYE);
     for (int k = 0; k < 12; ++k) ok = ok && std::isfinite(c.c2w[k]);
+    for (int k = 0; k < 3; ++k) ok = ok && std::isfinite(c.shutter[k]);
     if (!ok) return fail(RF_ERR_INVALID_ARG, "camera %d is invalid (size, intrinsics or pose)", index);
     return RF_OK;
 }
 
-rf_status check_opts(const rf_render_opts *o, float *eps, int32_t *max_steps) {
+rf_status check_opts(const rf_render_opts *o, float *eps, int32_t *max_steps, SphereFx *fx) {
     *eps = 1e-4f;
     *max_steps = kDefaultMaxSteps;
+    if (fx) memset(fx, 0, sizeof *fx);
     if (o) {
         if (!(o->eps >= 0.f) || !std::isfinite(o->eps))
             return fail(RF_ERR_INVALID_ARG, "opts.eps must be finite and >= 0");
         *eps = o->eps;
         if (o->max_steps > 0) *max_steps = o->max_steps;
+        if (o->max_bounces < 0) return fail(RF_ERR_INVALID_ARG, "opts.max_bounces must be >= 0");
+        if (o->max_bounces > 0) {
+            bool ok = o->sphere[3] > 0.f && std::isfinite(o->sphere[3]) && o->sphere_ior >= 0.f &&
+                      std::isfinite(o->sphere_ior);
+            for (int a = 0; a < 3; ++a) ok = ok && std::isfinite(o->sphere[a]);
+            if (!ok) return fail(RF_ERR_INVALID_ARG, "sphere needs a finite centre, radius > 0 and ior >= 0");
+            if (!fx) return fail(RF_ERR_INVALID_ARG, "this entry point does not support the sphere");
+            *fx = {o->sphere[0], o->sphere[1], o->sphere[2], o->sphere[3], o->sphere_ior, o->max_bounces};
+        }
     }
     return RF_OK;
 }

@@ -202,8 +202,10 @@ RF_API rf_status rf_serve_create(rf_scene *scene, const rf_serve_config *cfg, rf
                     kMaxCamsPerLaunch);
     float eps;
     int32_t max_steps;
-    rf_render_opts o{cfg->eps, cfg->max_steps, 0, 0};
-    rf_status rc = check_opts(&o, &eps, &max_steps);
+    rf_render_opts o{};
+    o.eps = cfg->eps;
+    o.max_steps = cfg->max_steps;
+    rf_status rc = check_opts(&o, &eps, &max_steps, nullptr);
     if (rc != RF_OK) return rc;
     rf_server *s = new rf_server();
     s->scene = scene;

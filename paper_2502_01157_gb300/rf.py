@@ -35,7 +35,8 @@ _DTYPES = {torch.float32: RF_F32, torch.bfloat16: RF_BF16, torch.float16: RF_F16
 class rf_camera(ctypes.Structure):
     _fields_ = [("c2w", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
-                ("height", ctypes.c_int32), ("t_near", ctypes.c_float), ("t_far", ctypes.c_float)]
+                ("height", ctypes.c_int32), ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
+                ("model", ctypes.c_int32), ("shutter", ctypes.c_float * 3)]
 
 
 class rf_scene_desc(ctypes.Structure):
@@ -49,7 +50,9 @@ class rf_scene_desc(ctypes.Structure):
 
 class rf_render_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("max_steps", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32),
+                ("max_bounces", ctypes.c_int32), ("sphere", ctypes.c_float * 4),
+                ("sphere_ior", ctypes.c_float)]
 
 
 class rf_serve_config(ctypes.Structure):
@@ -193,6 +196,8 @@ def camera_struct(cam) -> rf_camera:
     c.fx, c.fy, c.cx, c.cy = cam.fx, cam.fy, cam.cx, cam.cy
     c.width, c.height = int(cam.width), int(cam.height)
     c.t_near, c.t_far = cam.t_near, cam.t_far
+    c.model = int(getattr(cam, "model", 0))
+    c.shutter[:] = [float(v) for v in getattr(cam, "shutter", (0.0, 0.0, 0.0))]
     return c
 
 
@@ -204,10 +209,16 @@ def camera_array(cams) -> "ctypes.Array":
     return arr
 
 
-def opts_struct(eps: float = 1e-4, max_steps: int = 0) -> rf_render_opts:
+def opts_struct(eps: float = 1e-4, max_steps: int = 0, effects=None) -> rf_render_opts:
+    """Render options; ``effects`` is an analytic sphere with ``centre``,
+    ``radius``, ``ior`` (0: mirror) and ``max_bounces`` (e.g. ``scenes.Sphere``)."""
     o = rf_render_opts()
     o.eps = float(eps)
     o.max_steps = int(max_steps)
+    if effects is not None:
+        o.max_bounces = int(effects.max_bounces)
+        o.sphere[:] = [float(v) for v in effects.centre] + [float(effects.radius)]
+        o.sphere_ior = float(effects.ior)
     return o
 
 
@@ -306,10 +317,12 @@ class Foam:
             self.update_positions(pos.detach())
 
     def render(self, cams, eps: float = 1e-4, max_steps: int = 0, steps: bool = False,
-               status: bool = False, quantile: bool = False, out=None, stream=None) -> dict:
+               status: bool = False, quantile: bool = False, out=None, stream=None,
+               effects=None) -> dict:
         """Forward render; returns rgb [R,3], trans [R], depth [R] (+ steps,
         status; + quantile [R] and quantile_aux [R,5] with ``quantile``) as
-        CUDA tensors, rays of the cameras concatenated."""
+        CUDA tensors, rays of the cameras concatenated.  ``effects``: an
+        analytic sphere the rays reflect off or refract through."""
         ca = camera_array(cams)
         R = n_rays_of(cams)
         dev = self.pos.device
@@ -323,7 +336,7 @@ class Foam:
             if quantile:
                 out["quantile"] = torch.empty(R, device=dev)
                 out["quantile_aux"] = torch.empty(R, 5, device=dev)
-        o = opts_struct(eps, max_steps)
+        o = opts_struct(eps, max_steps, effects)
         fo = rf_fwd_outputs(_addr(out["rgb"]), _addr(out["trans"]), _addr(out["depth"]),
                             _addr(out.get("steps")), _addr(out.get("status")),
                             _addr(out.get("quantile")), _addr(out.get("quantile_aux")))
@@ -332,7 +345,8 @@ class Foam:
         return out
 
     def backward(self, cams, fwd: dict, d_rgb, d_trans=None, d_depth=None, grads=None,
-                 eps: float = 1e-4, max_steps: int = 0, d_quantile=None, stream=None) -> dict:
+                 eps: float = 1e-4, max_steps: int = 0, d_quantile=None, stream=None,
+                 effects=None) -> dict:
         """Accumulate gradients (density, sh, pos; float32) of the forward
         outputs (and of the quantile loss, with ``d_quantile``) into ``grads``
         (zero-initialised if None)."""
@@ -342,7 +356,7 @@ class Foam:
                          sh=torch.zeros(tuple(self.sh.shape), device=dev),
                          pos=torch.zeros(self.n_sites, 3, device=dev))
         ca = camera_array(cams)
-        o = opts_struct(eps, max_steps)
+        o = opts_struct(eps, max_steps, effects)
         bi = rf_bwd_inputs(_addr(fwd["rgb"]), _addr(fwd["trans"]), _addr(fwd.get("depth")),
                            _addr(fwd.get("quantile_aux")), _addr(d_rgb), _addr(d_trans),
                            _addr(d_depth), _addr(d_quantile))
@@ -352,13 +366,13 @@ class Foam:
         return grads
 
     def trace(self, cam, max_per_ray: int = 256, eps: float = 1e-4, max_steps: int = 0,
-              stream=None):
+              stream=None, effects=None):
         """Visited cells per ray [R, max_per_ray] (-1 padded) and counts [R]."""
         R = int(cam.width) * int(cam.height)
         dev = self.pos.device
         cells = torch.empty(R, max_per_ray, dtype=torch.int32, device=dev)
         counts = torch.empty(R, dtype=torch.int32, device=dev)
-        o = opts_struct(eps, max_steps)
+        o = opts_struct(eps, max_steps, effects)
         ca = camera_array([cam])
         _check(lib().rf_trace_cells(self.handle, ca, ctypes.byref(o), int(max_per_ray),
                                     _ptr(cells), _ptr(counts), _stream(stream)))
@@ -415,7 +429,7 @@ def mse_grad(rgb, target, scale: float, loss=None, stream=None):
 
 
 def render_noalloc(pos, adj_off, adj_idx, density, sh, aabb, cams, eps: float = 1e-4,
-                   max_steps: int = 0, out=None, stream=None) -> dict:
+                   max_steps: int = 0, out=None, stream=None, effects=None) -> dict:
     """``rf_render_fwd_noalloc``: forward render straight from the caller's
     arrays, with no device allocation inside the library (its only scratch is
     a fixed 64-camera array).  Same outputs as :meth:`Foam.render`."""
@@ -427,7 +441,7 @@ def render_noalloc(pos, adj_off, adj_idx, density, sh, aabb, cams, eps: float = 
                    depth=torch.empty(R, device=dev))
     K = int(sh.shape[1])
     box = (ctypes.c_float * 6)(*[float(v) for v in list(aabb[0]) + list(aabb[1])])
-    o = opts_struct(eps, max_steps)
+    o = opts_struct(eps, max_steps, effects)
     _check(lib().rf_render_fwd_noalloc(int(pos.shape[0]), int(adj_idx.shape[0]), _ptr(pos),
                                        _ptr(adj_off), _ptr(adj_idx) if adj_idx.numel() else None,
                                        _ptr(density), _ptr(sh), int(round(K ** 0.5)) - 1,
@@ -439,10 +453,11 @@ def render_noalloc(pos, adj_off, adj_idx, density, sh, aabb, cams, eps: float = 
 
 class _Render(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, foam, cams, eps, max_steps, quantile, density, sh, pos):
+    def forward(ctx, foam, cams, eps, max_steps, quantile, effects, density, sh, pos):
         foam._sync_positions(pos)
-        out = foam.render(cams, eps=eps, max_steps=max_steps, quantile=quantile)
+        out = foam.render(cams, eps=eps, max_steps=max_steps, quantile=quantile, effects=effects)
         ctx.foam, ctx.cams, ctx.eps, ctx.max_steps, ctx.quantile = foam, cams, eps, max_steps, quantile
+        ctx.effects = effects
         ctx.dtypes = (density.dtype, sh.dtype)
         if quantile:
             ctx.save_for_backward(out["rgb"], out["trans"], out["depth"], out["quantile_aux"])
@@ -458,11 +473,11 @@ class _Render(torch.autograd.Function):
         need = ctx.needs_input_grad
         dev = rgb.device
         grads = {}
-        if need[5]:
-            grads["density"] = torch.zeros(foam.n_sites, device=dev)
         if need[6]:
-            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+            grads["density"] = torch.zeros(foam.n_sites, device=dev)
         if need[7]:
+            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+        if need[8]:
             grads["pos"] = torch.zeros(foam.n_sites, 3, device=dev)
         if grads:
             z = lambda g: None if g is None else g.contiguous().float()
@@ -472,17 +487,18 @@ class _Render(torch.autograd.Function):
             foam.backward(ctx.cams, fwd,
                           z(g_rgb) if g_rgb is not None else torch.zeros_like(rgb),
                           z(g_trans), z(g_depth), grads=grads, eps=ctx.eps,
-                          max_steps=ctx.max_steps, d_quantile=z(g_quant) if ctx.quantile else None)
+                          max_steps=ctx.max_steps, d_quantile=z(g_quant) if ctx.quantile else None,
+                          effects=ctx.effects)
         gd = grads.get("density")
         gs = grads.get("sh")
-        return (None, None, None, None, None,
+        return (None, None, None, None, None, None,
                 None if gd is None else gd.to(ctx.dtypes[0]),
                 None if gs is None else gs.to(ctx.dtypes[1]),
                 grads.get("pos"))
 
 
 def render(foam: Foam, cams, density=None, sh=None, pos=None, eps: float = 1e-4,
-           max_steps: int = 0, quantile: bool = False):
+           max_steps: int = 0, quantile: bool = False, effects=None):
     """Differentiable render of ``cams``: returns (rgb [R,3], trans [R],
     depth [R]) and, with ``quantile``, the per-ray quantile loss of Eq. (6)
     [R]; gradients flow to ``density``, ``sh`` and ``pos`` (defaults: the
@@ -493,4 +509,4 @@ def render(foam: Foam, cams, density=None, sh=None, pos=None, eps: float = 1e-4,
         foam.set_attributes(density.detach(), sh.detach())
     if pos is None:
         pos = foam.pos
-    return _Render.apply(foam, cams, eps, max_steps, bool(quantile), density, sh, pos)
+    return _Render.apply(foam, cams, eps, max_steps, bool(quantile), effects, density, sh, pos)

@@ -49,3 +49,31 @@ def test_version_and_argument_errors_without_gpu(L):
     assert L.rf_scene_create(ctypes.byref(d), None, ctypes.byref(h)) == 1
     assert L.rf_render_fwd(None, None, 0, None, None, None, None, None, None, None) == 1
     assert L.rf_scene_destroy(None) == 0
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets (compiled with the host C compiler, no GPU)."""
+    structs = {n: getattr(rf, n) for n in ("rf_camera", "rf_scene_desc", "rf_render_opts",
+                                           "rf_serve_config", "rf_serve_metrics", "rf_fwd_outputs",
+                                           "rf_bwd_inputs", "rf_grads")}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
+    for n, cls in structs.items():
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{n} {f[0]} %zu\\n", offsetof({n}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    r = subprocess.run(["gcc", "-std=c11", str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        n, f, v = ln.split()
+        got[(n, f)] = int(v)
+    for n, cls in structs.items():
+        assert got[(n, "size")] == ctypes.sizeof(cls), n
+        for f in cls._fields_:
+            assert got[(n, f[0])] == getattr(cls, f[0]).offset, (n, f[0])

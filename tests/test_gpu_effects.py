@@ -1,0 +1,248 @@
+"""Ray-based effects (Fig. 2) on the GPU against the FP64 oracle: fisheye and
+rolling-shutter cameras, and an analytic mirror / glass sphere met in the
+same walk (forward images, visited cells, gradients, quantile loss)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2502_01157_gb300 import rf
+from paper_2502_01157_gb300 import scenes as S
+from tests.helpers import camera_at, random_scene
+from tests.parity import (GRAD_REL, assert_images_close, compare_traces, foam_of, gpu_render,
+                          rel_l2, rounded_scene)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    rf.lib()
+
+
+def _with(cam, **kw):
+    args = dict(c2w=cam.c2w, fx=cam.fx, fy=cam.fy, cx=cam.cx, cy=cam.cy, width=cam.width,
+                height=cam.height, t_near=cam.t_near, t_far=cam.t_far, model=cam.model,
+                shutter=cam.shutter)
+    args.update(kw)
+    return S.Camera(**args)
+
+
+def _cams():
+    fish = S.fisheye(41, 29, 230.0, c2w=S.look_at((0.05, -0.1, 0.02), (0.6, 0.5, 0.3)))
+    roll = _with(camera_at((0.2, 0.1, -0.3), (-0.5, 0.4, 0.9), w=35, h=23, fov=75.0),
+                 shutter=(0.35, -0.25, 0.15))
+    roll_fish = _with(S.fisheye(24, 18, 180.0, c2w=S.look_at((2.1, -1.6, 0.7), (0.0, 0.0, 0.0))),
+                      shutter=(-0.2, 0.3, 0.4))
+    pin = camera_at((-0.3, 0.2, 0.1), (1.0, 0.0, 0.2), w=19, h=13)
+    return [fish, roll, roll_fish, pin]
+
+
+def _per_camera(cams, fn):
+    base = 0
+    for cam in cams:
+        fn(cam, slice(base, base + cam.n_rays))
+        base += cam.n_rays
+
+
+@pytest.mark.parametrize("dt,deg", [("f32", 3), ("bf16", 2), ("f16", 0), ("f32", 1)])
+def test_camera_models_match_oracle(dt, deg):
+    sc = random_scene(3000, deg, 500 + deg)
+    cams = _cams()
+    foam = foam_of(sc, dt)
+    g = gpu_render(foam, cams)
+    ref = rounded_scene(sc, dt)
+
+    def check(cam, sl):
+        o = oracle.render(ref, cam, trace=512)
+        err = assert_images_close({k: v[sl] for k, v in g.items()}, o)
+        ok = ~o["degen"]
+        np.testing.assert_array_equal(g["steps"][sl][ok], o["steps"][ok])
+        cells, counts = foam.trace(cam, max_per_ray=512)
+        bad, nd = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 512)
+        print(f"{dt} deg {deg} model {cam.model} shutter {cam.shutter}: {err}, degenerate {nd}")
+        assert bad == 0
+
+    _per_camera(cams, check)
+    # a pinhole camera gives the same bits in a launch with effects as alone
+    alone = gpu_render(foam, [cams[-1]])
+    n = cams[-1].n_rays
+    for k in ("rgb", "trans", "depth", "steps"):
+        np.testing.assert_array_equal(alone[k], g[k][-n:])
+
+
+def _sphere_cams():
+    return [camera_at((-0.85, 0.3, 0.2), (0.1, 0.0, 0.05), w=37, h=29, fov=45.0),
+            S.fisheye(21, 17, 200.0, c2w=S.look_at((0.75, -0.5, 0.4), (0.1, 0.0, 0.05))),
+            _with(camera_at((0.1, 0.8, -0.6), (0.1, 0.0, 0.05), w=18, h=14, fov=50.0),
+                  shutter=(0.1, 0.0, 0.2))]
+
+
+SPHERES = {"mirror": S.Sphere((0.1, 0.0, 0.05), 0.35, ior=0.0, max_bounces=4),
+           "glass": S.Sphere((0.1, 0.0, 0.05), 0.35, ior=1.5, max_bounces=6),
+           "dense glass": S.Sphere((0.1, 0.0, 0.05), 0.45, ior=2.4, max_bounces=3),
+           # the first and third cameras sit inside this one
+           "camera inside": S.Sphere((-0.2, 0.1, 0.0), 1.0, ior=1.33, max_bounces=8)}
+
+
+@pytest.mark.parametrize("name", list(SPHERES))
+@pytest.mark.parametrize("dt,deg", [("f32", 3), ("bf16", 1)])
+def test_sphere_forward_and_backward_match_oracle(name, dt, deg):
+    sph = SPHERES[name]
+    sc = random_scene(2500, deg, 600 + deg)
+    cams = _sphere_cams()
+    foam = foam_of(sc, dt)
+    ref = rounded_scene(sc, dt)
+    out = foam.render(cams, steps=True, effects=sph)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    R = rf.n_rays_of(cams)
+    rng = np.random.default_rng(7)
+    gr = rng.normal(size=(R, 3)).astype(np.float32)
+    gt = rng.normal(size=R).astype(np.float32)
+    gd = rng.normal(size=R).astype(np.float32)
+    acc = dict(density=0, sh=0, pos=0)
+    n_bounced = [0]
+
+    def check(cam, sl):
+        o = oracle.render(ref, cam, trace=512, effects=sph)
+        err = assert_images_close({k: v[sl] for k, v in g.items()}, o)
+        ok = ~o["degen"]
+        np.testing.assert_array_equal(g["steps"][sl][ok], o["steps"][ok])
+        cells, counts = foam.trace(cam, max_per_ray=512, effects=sph)
+        bad, nd = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 512)
+        straight = oracle.render(ref, cam)
+        n_bounced[0] += int(np.sum(np.abs(straight["trans"] - o["trans"]) > 1e-6))
+        print(f"{name} {dt} deg {deg} cam {cam.model}: {err}, degenerate {nd}, traces bad {bad}")
+        assert bad == 0
+        for a in (gr, gt, gd):
+            a[sl][o["degen"]] = 0
+        G = oracle.render_bwd(ref, cam, gr[sl], gt[sl], gd[sl], effects=sph)
+        for k in acc:
+            acc[k] = acc[k] + G[k]
+
+    _per_camera(cams, check)
+    assert n_bounced[0] > R // 10   # the sphere really changes many rays
+    t = lambda a: torch.from_numpy(a).cuda()
+    G = foam.backward(cams, out, t(gr), t(gt), t(gd), effects=sph)
+    torch.cuda.synchronize()
+    for k in acc:
+        e = rel_l2(G[k].cpu().numpy(), acc[k])
+        print(f"  grad {k}: rel err {e:.2e}")
+        assert e <= GRAD_REL, k
+
+
+@pytest.mark.parametrize("name", ["mirror", "glass"])
+def test_sphere_with_quantile_loss(name):
+    sph = SPHERES[name]
+    sc = random_scene(2000, 1, 77)
+    cams = _sphere_cams()[:2]
+    foam = foam_of(sc)
+    out = foam.render(cams, quantile=True, effects=sph)
+    plain = foam.render(cams, effects=sph)
+    torch.cuda.synchronize()
+    for k in ("rgb", "trans", "depth"):
+        assert torch.equal(plain[k], out[k]), k
+    q = out["quantile"].cpu().numpy()
+    R = rf.n_rays_of(cams)
+    rng = np.random.default_rng(3)
+    gq = rng.normal(size=R).astype(np.float32)
+    acc = dict(density=0, pos=0)
+
+    def check(cam, sl):
+        qo = oracle.render_quantile(sc, cam, effects=sph)
+        err = np.sqrt(np.mean((q[sl] - qo) ** 2))
+        print(f"{name}: quantile rmse {err:.2e}")
+        assert err <= 1e-5
+        gq[sl][oracle.render(sc, cam, effects=sph)["degen"]] = 0
+        G = oracle.render_bwd(sc, cam, np.zeros((cam.n_rays, 3)), g_quantile=gq[sl], effects=sph)
+        for k in acc:
+            acc[k] = acc[k] + G[k]
+
+    _per_camera(cams, check)
+    G = foam.backward(cams, out, torch.zeros(R, 3, device="cuda"),
+                      d_quantile=torch.from_numpy(gq).cuda(), effects=sph)
+    torch.cuda.synchronize()
+    for k in acc:
+        e = rel_l2(G[k].cpu().numpy(), acc[k])
+        print(f"  quantile grad {k}: rel err {e:.2e}")
+        assert e <= GRAD_REL
+
+
+def test_sphere_autograd_and_zero_bounces():
+    sc = random_scene(1500, 2, 88)
+    foam = foam_of(sc)
+    cam = _sphere_cams()[0]
+    sph = SPHERES["glass"]
+    dens = foam.density.clone().requires_grad_(True)
+    pos = foam.pos.clone().requires_grad_(True)
+    rgb, tr, dp = rf.render(foam, [cam], dens, None, pos, effects=sph)
+    (rgb.sum() + tr.sum() + 0.1 * dp.sum()).backward()
+    fwd = foam.render([cam], effects=sph)
+    G = foam.backward([cam], fwd, torch.ones_like(fwd["rgb"]), torch.ones_like(fwd["trans"]),
+                      torch.full_like(fwd["depth"], 0.1), effects=sph)
+    torch.testing.assert_close(dens.grad, G["density"], rtol=1e-5, atol=1e-6)
+    torch.testing.assert_close(pos.grad, G["pos"], rtol=1e-5, atol=1e-6)
+    # no bounces allowed: the plain kernels' result
+    none = foam.render([cam], effects=S.Sphere((0.1, 0.0, 0.05), 0.35, max_bounces=0))
+    plain = foam.render([cam])
+    for k in ("rgb", "trans", "depth"):
+        assert torch.equal(none[k], plain[k])
+
+
+def test_noalloc_takes_fisheye_and_rejects_shutter_and_sphere():
+    sc = random_scene(1200, 1, 99)
+    foam = foam_of(sc)
+    fish = S.fisheye(20, 14, 190.0, c2w=S.look_at((0.1, 0.0, 0.0), (1.0, 0.2, 0.1)))
+    ref = foam.render([fish])
+    aabb = (sc.aabb_min, sc.aabb_max)
+    out = rf.render_noalloc(foam.pos, foam.adj_off, foam.adj_idx, foam.density, foam.sh, aabb, [fish])
+    torch.cuda.synchronize()
+    for k in ("rgb", "trans", "depth"):
+        assert torch.equal(out[k], ref[k]), k
+    roll = _with(fish, shutter=(0.1, 0.0, 0.0))
+    with pytest.raises(RuntimeError, match="rolling shutter"):
+        rf.render_noalloc(foam.pos, foam.adj_off, foam.adj_idx, foam.density, foam.sh, aabb, [roll])
+    with pytest.raises(RuntimeError, match="sphere"):
+        rf.render_noalloc(foam.pos, foam.adj_off, foam.adj_idx, foam.density, foam.sh, aabb, [fish],
+                          effects=SPHERES["mirror"])
+
+
+def test_invalid_effects_are_rejected():
+    sc = random_scene(500, 0, 5)
+    foam = foam_of(sc)
+    cam = camera_at((0.0, 0.0, 0.0), (1.0, 0.0, 0.0), w=4, h=4)
+    with pytest.raises(RuntimeError):
+        foam.render([cam], effects=S.Sphere((0, 0, 0), 0.0))
+    with pytest.raises(RuntimeError):
+        foam.render([cam], effects=S.Sphere((0, 0, 0), 0.3, ior=-1.0))
+    with pytest.raises(RuntimeError):
+        foam.render([_with(cam, model=7)])
+
+
+def test_full_size_c3_fisheye_rolling_shutter_glass_sphere_sampled():
+    sc = S.config_scene("c3")
+    base = S.config_cameras("c3")[0]
+    cam = _with(S.fisheye(base.width, base.height, 200.0, c2w=base.c2w), shutter=(0.02, 0.0, 0.01))
+    sph = S.Sphere((0.0, 0.0, 0.5), 0.25, ior=1.5, max_bounces=4)
+    foam = foam_of(sc)
+    out = foam.render([cam], effects=sph)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    px = np.sort(rng.choice(cam.n_rays, size=500, replace=False))
+    o = oracle.render(sc, cam, pixels=px, effects=sph)
+    g = {k: out[k].cpu().numpy()[px] for k in ("rgb", "trans", "depth")}
+    err = assert_images_close(g, o)
+    print(f"c3 fisheye + shutter + glass: {err}, degenerate {int(o['degen'].sum())}")
+    keep = px[~o["degen"]]
+    gr = np.zeros((cam.n_rays, 3), np.float32)
+    gr[keep] = rng.normal(size=(len(keep), 3))
+    G = foam.backward([cam], out, torch.from_numpy(gr).cuda(), effects=sph)
+    torch.cuda.synchronize()
+    Go = oracle.render_bwd(sc, cam, gr[keep], pixels=keep, effects=sph)
+    for k in ("density", "sh", "pos"):
+        e = rel_l2(G[k].cpu().numpy(), Go[k])
+        print(f"c3 effects grad {k}: rel err {e:.2e}")
+        assert e <= GRAD_REL
