@@ -237,6 +237,53 @@ def run_reference(args):
 SERVE_RATES = (50, 200, 1000, 2000)
 
 
+def effects_extras(S, rf, foam, cam, target, scale, loss, grads, args, dev):
+    """Ray-based effects (Fig. 2) on the main workload's scene and image size:
+    a 200-degree equidistant fisheye, a rolling shutter, and a clear-glass and a
+    mirror sphere of radius 0.25 in front of the camera (FP32 attributes)."""
+    import numpy as np
+    import torch
+
+    R = cam.n_rays
+    fish = S.fisheye(cam.width, cam.height, 200.0, c2w=cam.c2w)
+    roll = S.Camera(cam.c2w, cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height,
+                    shutter=(0.02, 0.0, 0.01))
+    centre = tuple(np.asarray(cam.c2w, np.float64) @ np.array([0.0, 0.0, 0.5, 1.0]))
+    glass = S.Sphere(centre, 0.25, ior=1.5, max_bounces=4)
+    mirror = S.Sphere(centre, 0.25, ior=0.0, max_bounces=4)
+    out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
+               depth=torch.empty(R, device=dev))
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    res = {"recipe": "c3 scene, 1920x1080: fisheye 200 deg; rolling shutter (0.02, 0, 0.01) over the "
+                     "frame; glass (n = 1.5) / mirror sphere r = 0.25 at 0.5 along the view axis"}
+    for name, c, sph in (("fisheye", fish, None), ("rolling_shutter", roll, None),
+                         ("glass_sphere", cam, glass), ("mirror_sphere", cam, mirror),
+                         ("fisheye_glass", fish, glass)):
+        def fstep():
+            foam.render([c], out=out, effects=sph)
+            d_rgb, _ = rf.mse_grad(out["rgb"], target, scale, loss)
+            foam.backward([c], out, d_rgb, grads=grads, effects=sph)
+
+        chk = foam.render([c], steps=True, effects=sph)
+        k = float(chk["steps"].float().mean().item())
+        for _ in range(2):
+            fstep()
+        torch.cuda.synchronize()
+        a, b, e = ev(), ev(), ev()
+        a.record()
+        for _ in range(args.steps):
+            foam.render([c], out=out, effects=sph)
+        b.record()
+        for _ in range(args.steps):
+            fstep()
+        e.record()
+        torch.cuda.synchronize()
+        res[name] = {"fwd_mrays_s": R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6,
+                     "fwdbwd_mrays_s": R / (b.elapsed_time(e) / args.steps * 1e-3) / 1e6,
+                     "cell_steps_per_ray": k}
+    return res
+
+
 def mixture_extras(scene, args, dev):
     """The 3M-site mixture scene: 8 mixed-resolution cameras forward+backward
     in one launch (FP32), batched forward FP32 vs BF16 on the serving poses,
@@ -471,6 +518,7 @@ def main():
         barrier()
         res["fwd_quantile_fp32_mrays_s"] = R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
         res["fwdbwd_quantile_fp32_mrays_s"] = R / (b.elapsed_time(c) / args.steps * 1e-3) / 1e6
+        res["effects"] = effects_extras(S, rf, foam, cam, target, scale, loss, grads, args, dev)
 
     mixture = None
     if mix_scene is not None:
