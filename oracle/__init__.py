@@ -28,6 +28,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rf_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "adjacency.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "librf_oracle.so")
 _lock = threading.Lock()
@@ -46,10 +47,10 @@ def build(force: bool = False) -> str:
     """Compile rf_oracle.c into a shared library (gcc, -O2, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", *_SRCS, "-o", tmp, "-lm"]
     r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
     if r.returncode != 0:  # no OpenMP runtime: build serial
         r = subprocess.run(base, capture_output=True, text=True)
@@ -83,6 +84,9 @@ def lib():
                                               ctypes.c_int, _d, _d, ctypes.c_int]
             L.orc_render_quantile.restype = ctypes.c_int
             L.orc_render_bwd.restype = ctypes.c_int
+            L.orc_voronoi_faces.argtypes = [ctypes.c_int64, _d, ctypes.c_int64, _i64, _i64, _i64, _d,
+                                             _d, _d, ctypes.c_int]
+            L.orc_voronoi_faces.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = ctypes.c_int
             _lib = L
