@@ -416,6 +416,57 @@ RF_API rf_status rf_sample_multinomial(const float *weights, int64_t n, const fl
                                        void *stream);
 
 /*
+ * GPU Voronoi adjacency: the neighbour lists N(i) the walk traverses (the
+ * Delaunay graph of the sites), built from the positions alone and rebuilt
+ * whenever they move (the paper keeps this adjacency through training and
+ * updates it after position steps: the "Voronoi optimization" paragraph of
+ * Sec. 4, with the tracing of Sec. 3.2).
+ *
+ * j is a neighbour of i iff their Voronoi cells share a face of positive area
+ * inside the domain box (the part of the bisector plane of p_i and p_j that
+ * is no farther from them than from any other site).  Each cell is built on
+ * the GPU as the domain box cut by the bisector half-spaces of nearby sites;
+ * every inside/outside decision is the FP64 one.  The lists are symmetric,
+ * sorted by neighbour id, without self loops: ready for rf_scene_desc.
+ *
+ * rf_adjacency_build: pos device float [n_sites][3]; domain6 HOST float[6]
+ *   (min xyz, max xyz) holding every site, or NULL for the sites' bounding
+ *   box grown by 5% of its extent (at least 1e-3) on every side.  Faces that
+ *   lie entirely outside the domain are not produced, so the domain should
+ *   hold the cameras as well as the sites.  incremental = 1 seeds each cell
+ *   with its previous neighbours (the sites moved a little since the last
+ *   build of the same n_sites); the result is the same as a full build.  The
+ *   call waits for the GPU three times (sites' box, edge count, completion).
+ *   Errors: RF_ERR_INVALID_ARG (bad sizes, non-finite positions, a site
+ *   outside domain6), RF_ERR_OOM, RF_ERR_BAD_SCENE (too many one-sided edges:
+ *   heavily degenerate sites).
+ * rf_adjacency_result: device pointers to the CSR (adj_off [n_sites + 1],
+ *   adj_idx [n_edges]) owned by the handle and valid until its next build or
+ *   destroy, and statistics (host).
+ */
+typedef struct rf_adjacency rf_adjacency;
+typedef struct rf_adjacency_stats {
+    int64_t n_sites, n_edges;
+    int64_t edges_before_symmetry;  /* directed edges the cells produced */
+    int64_t asym_added;             /* reverse edges added for symmetry */
+    int64_t wide_sites;             /* cells rebuilt with room for up to 186 faces */
+    int64_t failed_sites;           /* cells that could not be built (empty rows) */
+    int64_t fp64_tests;             /* vertex tests decided in FP64 */
+    int32_t max_degree;
+    int32_t reserved;
+    float domain[6];
+} rf_adjacency_stats;
+RF_API rf_status rf_adjacency_create(rf_adjacency **out);
+RF_API rf_status rf_adjacency_build(rf_adjacency *adj, int64_t n_sites, const float *pos,
+                                    const float *domain6, int32_t incremental, void *stream);
+RF_API rf_status rf_adjacency_result(rf_adjacency *adj, const int32_t **adj_off,
+                                     const int32_t **adj_idx, rf_adjacency_stats *stats);
+/* Copies the CSR into caller device arrays (adj_off [n_sites + 1], adj_idx
+ * [n_edges]), asynchronously on stream. */
+RF_API rf_status rf_adjacency_copy(rf_adjacency *adj, int32_t *adj_off, int32_t *adj_idx, void *stream);
+RF_API rf_status rf_adjacency_destroy(rf_adjacency *adj);
+
+/*
  * MSE loss helper for a training step (device, n = 3 * rays):
  *   d_rgb[k] = 2 * scale * (rgb[k] - target[k]);  *loss += scale * sum_k (rgb[k]-target[k])^2
  * loss is a device float accumulated with atomics (zero it first).

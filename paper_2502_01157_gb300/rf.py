@@ -87,6 +87,14 @@ class rf_grads(ctypes.Structure):
     _fields_ = [("density", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("pos", ctypes.c_void_p)]
 
 
+class rf_adjacency_stats(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("edges_before_symmetry", ctypes.c_int64), ("asym_added", ctypes.c_int64),
+                ("wide_sites", ctypes.c_int64), ("failed_sites", ctypes.c_int64),
+                ("fp64_tests", ctypes.c_int64), ("max_degree", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("domain", ctypes.c_float * 6)]
+
+
 class RFError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"rf error {code}: {msg}")
@@ -121,6 +129,13 @@ SIGNATURES = {
     "rf_trace_cells": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.POINTER(rf_render_opts),
                             ctypes.c_int32, _P, _P, _P]),
     "rf_mse_grad": (_S, [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
+    "rf_adjacency_create": (_S, [ctypes.POINTER(_P)]),
+    "rf_adjacency_build": (_S, [_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                                _P]),
+    "rf_adjacency_result": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                 ctypes.POINTER(rf_adjacency_stats)]),
+    "rf_adjacency_copy": (_S, [_P, _P, _P, _P]),
+    "rf_adjacency_destroy": (_S, [_P]),
     "rf_serve_create": (_S, [_P, ctypes.POINTER(rf_serve_config), ctypes.POINTER(_P)]),
     "rf_serve_submit": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.POINTER(ctypes.c_uint64)]),
     "rf_serve_poll": (_S, [_P, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_int32),
@@ -283,6 +298,16 @@ class Foam:
                    t(scene.sh, attr_dtype),
                    aabb=(scene.aabb_min, scene.aabb_max), stream=stream)
 
+    @classmethod
+    def from_sites(cls, pos, density, sh, domain=None, aabb=None, adjacency=None, stream=None):
+        """A foam whose neighbour lists are built on the GPU from ``pos`` (an
+        :class:`Adjacency` may be passed to reuse its buffers)."""
+        builder = adjacency if adjacency is not None else Adjacency()
+        off, idx = builder.build(pos, domain=domain, stream=stream)
+        foam = cls(pos, off, idx, density, sh, aabb=aabb, stream=stream)
+        foam.adjacency_stats = builder.stats
+        return foam
+
     @property
     def handle(self):
         if self._h is None:
@@ -394,6 +419,48 @@ class Foam:
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().rf_scene_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Adjacency:
+    """GPU Voronoi adjacency builder (``rf_adjacency_*``): the neighbour lists
+    the walk needs, from the site positions alone."""
+
+    def __init__(self):
+        h = _P()
+        _check(lib().rf_adjacency_create(ctypes.byref(h)))
+        self._h = h
+        self.stats = None
+
+    def build(self, pos, domain=None, incremental: bool = False, stream=None):
+        """Returns (adj_off [N+1], adj_idx [E]) int32 CUDA tensors and keeps the
+        build statistics in ``self.stats``; ``domain`` = (min xyz, max xyz)."""
+        if self._h is None:
+            raise RuntimeError("adjacency builder is closed")
+        pos = pos.contiguous().float()
+        n = int(pos.shape[0])
+        dom = None if domain is None else (ctypes.c_float * 6)(*[float(v) for v in np.ravel(domain)])
+        _check(lib().rf_adjacency_build(self._h, n, _ptr(pos), dom, int(bool(incremental)),
+                                        _stream(stream)))
+        st = rf_adjacency_stats()
+        _check(lib().rf_adjacency_result(self._h, None, None, ctypes.byref(st)))
+        self.stats = {f[0]: (list(getattr(st, f[0])) if f[0] == "domain" else getattr(st, f[0]))
+                      for f in st._fields_ if f[0] != "reserved"}
+        off = torch.empty(n + 1, dtype=torch.int32, device=pos.device)
+        idx = torch.empty(max(int(st.n_edges), 1), dtype=torch.int32, device=pos.device)[: int(st.n_edges)]
+        _check(lib().rf_adjacency_copy(self._h, _ptr(off), _ptr(idx) if st.n_edges else None,
+                                       _stream(stream)))
+        return off, idx
+
+    def close(self):
+        if self._h is not None:
+            lib().rf_adjacency_destroy(self._h)
             self._h = None
 
     def __del__(self):
