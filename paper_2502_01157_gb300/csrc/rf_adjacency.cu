@@ -28,7 +28,7 @@
 namespace rf {
 namespace {
 
-constexpr int kWarps = 8;             // sites (warps) per block, normal pass
+constexpr int kWarps = 4;             // sites (warps) per block, normal pass
 constexpr int kMaxPlanes = 64;        // normal pass: 6 box planes + up to 58 sites
 constexpr int kWideWarps = 2;
 constexpr int kWideMaxPlanes = 192;   // second pass for the cells that overflowed
@@ -72,6 +72,7 @@ struct CellSmem {
     float4 vtx[2 * MAXP];                // vertex x, y, z and its FP32 error bound
     uint32_t ebits[MAXP * (MAXP / 32)];  // directed edges of the removed triangles
     uint32_t src_seen[MAXP / 32];        // boundary-edge sources seen in this cut
+    float vlen[2 * MAXP];                // |vertex|
     uint8_t nxt[MAXP];                   // boundary cycle: a -> nxt[a]
     uint8_t cyc[MAXP];
 };
@@ -158,13 +159,14 @@ struct Cell {
 
     __device__ void update_radius() {
         float r = 0.f;
-        for (int t = lane; t < n_tri; t += 32) {
-            const float4 v = m.vtx[t];
-            const float d = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z) + v.w;
-            r = fmaxf(r, d * d);
-        }
-        for (int o = 16; o; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-        R2 = r * (1.f + 1e-5f);
+        for (int t = lane; t < n_tri; t += 32) r = fmaxf(r, m.vlen[t] + m.vtx[t].w);
+        r = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r)));  // r >= 0
+        R2 = r * r * (1.f + 1e-5f);
+    }
+
+    __device__ __forceinline__ void put_vertex(int t, const float4 &v) {
+        m.vtx[t] = v;
+        m.vlen[t] = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
     }
 
     // The domain box about the site: slots 0..5 = +x, -x, +y, -y, +z, -z.
@@ -194,7 +196,7 @@ struct Cell {
             // det(n_X, n_Y, n_Z) = (-1)^(sx+sy+sz): keep det > 0 (counter-clockwise seen from outside)
             const bool pos = ((sx + sy + sz) & 1) == 0;
             m.tri[lane] = pos ? (X | Y << 8 | Z << 16) : (X | Z << 8 | Y << 16);
-            m.vtx[lane] = vertex_of(m.pl[X], m.pl[pos ? Y : Z], m.pl[pos ? Z : Y]);
+            put_vertex(lane, vertex_of(m.pl[X], m.pl[pos ? Y : Z], m.pl[pos ? Z : Y]));
         }
         n_tri = 8;
         __syncwarp();
@@ -244,8 +246,7 @@ struct Cell {
             if (t < n_tri) {
                 const float4 v = m.vtx[t];
                 const float s = Q.x * v.x + Q.y * v.y + Q.z * v.z - Q.w;
-                const float vl = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
-                const float bound = 2.f * (nq * v.w + 4.f * 5.96e-8f * (nq * vl + Q.w));
+                const float bound = 2.f * (nq * v.w + 4.f * 5.96e-8f * (nq * m.vlen[t] + Q.w));
                 if (fabsf(s) > bound) {
                     out = s > 0.f;
                 } else {
@@ -341,16 +342,19 @@ struct Cell {
             const unsigned keep = ~rem[c] & valid;
             uint32_t tv = 0;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            float vl = 0.f;
             const bool mine = (keep >> lane) & 1u;
             if (mine) {
                 tv = m.tri[t];
                 v = m.vtx[t];
+                vl = m.vlen[t];
             }
             __syncwarp();
             if (mine) {
                 const int dst = kept + __popc(keep & ((1u << lane) - 1u));
                 m.tri[dst] = tv;
                 m.vtx[dst] = v;
+                m.vlen[dst] = vl;
             }
             kept += __popc(keep);
             __syncwarp();
@@ -363,25 +367,56 @@ struct Cell {
         for (int j = lane; j < L; j += 32) {
             const uint32_t a = m.cyc[j], b = m.cyc[(j + 1) % L];
             m.tri[kept + j] = a | b << 8 | (uint32_t)q << 16;
-            m.vtx[kept + j] = vertex_of(m.pl[a], m.pl[b], Q);
+            put_vertex(kept + j, vertex_of(m.pl[a], m.pl[b], Q));
         }
         n_tri = kept + L;
         __syncwarp();
-        // 7. planes that no vertex uses any more are redundant: free them
+        // 7. planes that no vertex uses any more are redundant: free them;
+        //    and the new radius
         uint32_t used[PW];
         for (int w = 0; w < PW; ++w) used[w] = 0u;
+        float r = 0.f;
         for (int t = lane; t < n_tri; t += 32) {
             const uint32_t tv = m.tri[t];
             const uint32_t e[3] = {tv & 255, (tv >> 8) & 255, (tv >> 16) & 255};
 #pragma unroll
             for (int j = 0; j < 3; ++j) used[e[j] >> 5] |= 1u << (e[j] & 31);
+            r = fmaxf(r, m.vlen[t] + m.vtx[t].w);
         }
         for (int w = 0; w < PW; ++w) {
-            for (int o = 16; o; o >>= 1) used[w] |= __shfl_xor_sync(full, used[w], o);
+            used[w] = __reduce_or_sync(full, used[w]);
             if (!((used[w] >> lane) & 1u)) m.pid[w * 32 + lane] = kFreeSlot;
         }
+        r = __uint_as_float(__reduce_max_sync(full, __float_as_uint(r)));
+        R2 = r * r * (1.f + 1e-5f);
         __syncwarp();
-        update_radius();
+    }
+
+    // Every site not seen yet lies outside the block of grid cells c - s ..
+    // c + s (the grid's own faces bound nothing: no site lies beyond).  A site
+    // cuts the cell only if it lies inside the ball about some vertex v with
+    // radius |v| (it is then closer to v than the site is), so the cell is
+    // final once every such ball lies in the block.
+    __device__ bool final_within(const int *c, const float3 &p, int s) {
+        const float h = P.g.h, mg = 1e-5f * h;
+        float blo[3], bhi[3];
+        bool all = true;
+        for (int a = 0; a < 3; ++a) {
+            const float pa = a == 0 ? p.x : a == 1 ? p.y : p.z;
+            blo[a] = c[a] - s > 0 ? P.g.lo[a] + (float)(c[a] - s) * h - pa + mg : -__int_as_float(0x7f800000);
+            bhi[a] = c[a] + s < P.g.dims[a] - 1 ? P.g.lo[a] + (float)(c[a] + s + 1) * h - pa - mg
+                                                 : __int_as_float(0x7f800000);
+            all = all && c[a] - s <= 0 && c[a] + s >= P.g.dims[a] - 1;
+        }
+        if (all) return true;  // the block covers the grid
+        bool inside = true;
+        for (int t = lane; t < n_tri; t += 32) {
+            const float4 v = m.vtx[t];
+            const float r = m.vlen[t] + 2.f * v.w;
+            inside = inside && v.x - r >= blo[0] && v.x + r <= bhi[0] && v.y - r >= blo[1] && v.y + r <= bhi[1] &&
+                     v.z - r >= blo[2] && v.z + r <= bhi[2];
+        }
+        return __all_sync(0xffffffffu, inside);
     }
 
     // Offer one candidate per lane; cut by the qualifying ones nearest first.
@@ -404,8 +439,8 @@ struct Cell {
     }
 };
 
-template <int MAXP, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) cell_kernel(const CellParams P) {
+template <int MAXP, int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) cell_kernel(const CellParams P) {
     __shared__ CellSmem<MAXP> smem[WARPS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
@@ -438,13 +473,26 @@ __global__ void __launch_bounds__(32 * WARPS) cell_kernel(const CellParams P) {
             c[a] = v < 0 ? 0 : v >= P.g.dims[a] ? P.g.dims[a] - 1 : v;
         }
         const int smax = max(P.g.dims[0], max(P.g.dims[1], P.g.dims[2]));
+        const float h = P.g.h;
         for (int s = 0; s <= smax && cell.status == kCellOk; ++s) {
             for (int dz = -s; dz <= s && cell.status == kCellOk; ++dz) {
                 const int z = c[2] + dz;
                 if (z < 0 || z >= P.g.dims[2]) continue;
+                // distance from the site to the slab of cell layer z
+                const float zl = P.g.lo[2] + (float)z * h - p.z, zh = zl + h;
+                const float gz = fmaxf(0.f, fmaxf(zl, -zh));
                 for (int dy = -s; dy <= s && cell.status == kCellOk; ++dy) {
                     const int y = c[1] + dy;
                     if (y < 0 || y >= P.g.dims[1]) continue;
+                    const float yl = P.g.lo[1] + (float)y * h - p.y, yh = yl + h;
+                    const float gy = fmaxf(0.f, fmaxf(yl, -yh));
+                    // only sites closer than 2 R can cut the cell: skip the row,
+                    // or keep the cells of the row that reach the 2 R ball
+                    const float reach2 = 4.f * cell.R2 - gy * gy - gz * gz;
+                    if (!(reach2 > 0.f)) continue;
+                    const float w = sqrtf(reach2) + 1e-5f * h;
+                    const int rx0 = (int)floorf((p.x - w - P.g.lo[0]) * P.g.inv_h);
+                    const int rx1 = (int)floorf((p.x + w - P.g.lo[0]) * P.g.inv_h);
                     const bool face = dz == -s || dz == s || dy == -s || dy == s;
                     // a full row of the shell, or its two end cells
                     for (int part = 0; part < (face ? 1 : 2); ++part) {
@@ -454,10 +502,9 @@ __global__ void __launch_bounds__(32 * WARPS) cell_kernel(const CellParams P) {
                             x1 = c[0] + s;
                         } else {
                             x0 = x1 = part == 0 ? c[0] - s : c[0] + s;
-                            if (s == 0 && part == 1) break;
                         }
-                        x0 = max(x0, 0);
-                        x1 = min(x1, P.g.dims[0] - 1);
+                        x0 = max(max(x0, 0), rx0);
+                        x1 = min(min(x1, P.g.dims[0] - 1), rx1);
                         if (x0 > x1) continue;
                         const int64_t row = ((int64_t)z * P.g.dims[1] + y) * P.g.dims[0];
                         const int32_t b = P.g.cell_start[row + x0], e = P.g.cell_start[row + x1 + 1];
@@ -472,15 +519,7 @@ __global__ void __launch_bounds__(32 * WARPS) cell_kernel(const CellParams P) {
                     }
                 }
             }
-            // every site not seen yet lies outside the block of cells c - s .. c + s
-            float rho = __int_as_float(0x7f800000);
-            for (int a = 0; a < 3; ++a) {
-                if (c[a] - s > 0) rho = fminf(rho, pc[a] - (P.g.lo[a] + (float)(c[a] - s) * P.g.h));
-                if (c[a] + s < P.g.dims[a] - 1) rho = fminf(rho, P.g.lo[a] + (float)(c[a] + s + 1) * P.g.h - pc[a]);
-            }
-            if (!(rho < __int_as_float(0x7f800000))) break;  // the block covers the grid
-            rho -= 1e-5f * P.g.h;
-            if (rho > 0.f && 4.f * cell.R2 <= rho * rho) break;
+            if (cell.final_within(c, p, s)) break;
         }
         // the neighbours: site planes still holding a vertex
         if (cell.status == kCellOk) {
@@ -898,13 +937,13 @@ RF_API rf_status rf_adjacency_build(rf_adjacency *a, int64_t n, const float *pos
         P.counters = a->counters;
         P.wide_list = a->wide;
         const int64_t blocks = std::min<int64_t>((n + kWarps - 1) / kWarps, 152 * 256);
-        cell_kernel<kMaxPlanes, kWarps><<<(unsigned)blocks, 32 * kWarps, 0, st>>>(P);
+        cell_kernel<kMaxPlanes, kWarps, 6><<<(unsigned)blocks, 32 * kWarps, 0, st>>>(P);
         RF_CUDA(cudaGetLastError());
         // the cells that overflowed, again with room for more faces
         P.site_list = a->wide;
         P.n_list = a->counters + 1;
         P.wide_list = nullptr;
-        cell_kernel<kWideMaxPlanes, kWideWarps><<<152 * 8, 32 * kWideWarps, 0, st>>>(P);
+        cell_kernel<kWideMaxPlanes, kWideWarps, 1><<<152 * 8, 32 * kWideWarps, 0, st>>>(P);
         RF_CUDA(cudaGetLastError());
         RF_CUDA(cudaMemcpyAsync(a->host, a->counters, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, st));
         RF_CUDA(cudaStreamSynchronize(st));
