@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--sites", type=int, default=0, help="override the workload's site count")
     ap.add_argument("--no-extras", action="store_true", help="skip dtype variants / serving")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjacency-only", action="store_true",
+                    help="time only the GPU adjacency build of --sites uniform sites (profiling)")
     return ap.parse_args()
 
 
@@ -195,6 +197,28 @@ def cpu_baseline(scene, cam, target, budget_s=12.0):
                       f"{cam.width}x{cam.height} view, {dt:.1f} s"}
 
 
+def cpu_adjacency_baseline(pos, budget_s=6.0):
+    """The FP64 adjacency oracle (face polygons, k-d tree candidates) on a
+    growing random sample of sites of the same scene."""
+    import numpy as np
+    import oracle
+    from oracle import adjacency as A
+
+    rng = np.random.default_rng(12)
+    n = 2000
+    while True:
+        sites = rng.choice(len(pos), size=min(n, len(pos)), replace=False)
+        t = time.perf_counter()
+        A.voronoi_neighbors(pos, sites=sites)
+        dt = time.perf_counter() - t
+        if dt >= budget_s or n >= len(pos):
+            break
+        n = int(n * min(8.0, max(2.0, budget_s / max(dt, 1e-3))))
+    return {"value": len(sites) / dt / 1e6, "unit": "Msites/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"FP64 face-polygon adjacency of {len(sites)} random sites of the "
+                                        f"{len(pos)}-site scene, {dt:.1f} s"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -284,6 +308,49 @@ def effects_extras(S, rf, foam, cam, target, scale, loss, grads, args, dev):
     return res
 
 
+def adjacency_extras(rf, scene, mix_scene, args, dev):
+    """GPU Voronoi adjacency (the neighbour lists the walk needs) of the main
+    scene and of the 3M-site mixture: a full build, and an incremental rebuild
+    after every site moved by a tenth of the mean spacing (default domain:
+    the sites' box grown by 5%).  Each build includes its three waits for the
+    GPU; times are the median of the repetitions."""
+    import statistics
+
+    import torch
+
+    out = {}
+    b = rf.Adjacency()
+    try:
+        for name, sc in (("main", scene), ("mixture_3m", mix_scene)):
+            if sc is None:
+                continue
+            pos = torch.from_numpy(sc.pos).to(dev)
+            spacing = float(torch.prod(pos.max(0).values - pos.min(0).values) / len(pos)) ** (1 / 3)
+            moved = pos + (0.1 * spacing) * torch.randn(pos.shape, device=dev,
+                                                        generator=torch.Generator(dev).manual_seed(3))
+
+            def timed(fn, reps):
+                ts = []
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    fn()
+                    torch.cuda.synchronize()
+                    ts.append((time.perf_counter() - t) * 1e3)
+                return statistics.median(ts)
+
+            full = timed(lambda: b.build(pos), 3)
+            st = dict(b.stats)
+            inc = timed(lambda: (b.build(pos), b.build(moved, incremental=True)), 2) - full
+            out[name] = {"n_sites": len(pos), "full_build_ms": full, "msites_s": len(pos) / full / 1e3,
+                         "incremental_ms": inc, "n_edges": st["n_edges"], "max_degree": st["max_degree"],
+                         "fp64_tests": st["fp64_tests"], "wide_sites": st["wide_sites"],
+                         "failed_sites": st["failed_sites"]}
+    finally:
+        b.close()
+    return out
+
+
 def mixture_extras(scene, args, dev):
     """The 3M-site mixture scene: 8 mixed-resolution cameras forward+backward
     in one launch (FP32), batched forward FP32 vs BF16 on the serving poses,
@@ -369,10 +436,39 @@ def mixture_extras(scene, args, dev):
     return res
 
 
+def run_adjacency_only(args):
+    """GPU adjacency of --sites (default 3M) sites uniform in [-1,1]^3 (seed 7),
+    default domain: --warmup untimed and --steps timed builds, one JSON line."""
+    import statistics
+
+    import numpy as np
+    import torch
+    from paper_2502_01157_gb300 import rf
+    from paper_2502_01157_gb300 import scenes as S
+
+    n = args.sites or 3_000_000
+    pos = torch.from_numpy(S.uniform_sites(n, -1.0, 1.0, np.random.default_rng(7))).cuda()
+    b = rf.Adjacency()
+    ts = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        b.build(pos)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ts.append((time.perf_counter() - t) * 1e3)
+    ms = statistics.median(ts)
+    print(json.dumps({"metric": "GPU Voronoi adjacency build", "value": n / ms / 1e3, "unit": "Msites/s",
+                      "ms_per_build": ms, "n_sites": n, "stats": b.stats}), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjacency_only:
+        return run_adjacency_only(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -519,6 +615,7 @@ def main():
         res["fwd_quantile_fp32_mrays_s"] = R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
         res["fwdbwd_quantile_fp32_mrays_s"] = R / (b.elapsed_time(c) / args.steps * 1e-3) / 1e6
         res["effects"] = effects_extras(S, rf, foam, cam, target, scale, loss, grads, args, dev)
+        res["adjacency"] = adjacency_extras(rf, scene, mix_scene, args, dev)
 
     mixture = None
     if mix_scene is not None:
@@ -587,6 +684,8 @@ def main():
                     "d2h_bytes_per_step": int(pin_rgb.numel() * 4 + 4)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, cam, target_np)
+        if not args.no_extras:
+            line["cpu_baseline"]["adjacency"] = cpu_adjacency_baseline(scene.pos)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
