@@ -39,6 +39,12 @@ constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanItems;
 
 enum : int32_t { kCellOk = 0, kCellOverflow = 1, kCellBroken = 2 };
 
+// The (dz, dy) rows of the blocks of shells 0..3 sorted by dz^2 + dy^2 (then
+// dz, dy): nearer rows first, so the first cuts come from nearer sites.
+__constant__ int8_t kRowOrder[84][2] = {{0, 0}, {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}, {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}, {-2, 0}, {0, -2}, {0, 2}, {2, 0}, {-2, -1}, {-2, 1}, {-1, -2}, {-1, 2}, {1, -2}, {1, 2}, {2, -1}, {2, 1}, {-2, -2}, {-2, 2}, {2, -2}, {2, 2}, {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}, {-2, 0}, {0, -2}, {0, 2}, {2, 0}, {-2, -1}, {-2, 1}, {-1, -2}, {-1, 2}, {1, -2}, {1, 2}, {2, -1}, {2, 1}, {-2, -2}, {-2, 2}, {2, -2}, {2, 2}, {-3, 0}, {0, -3}, {0, 3}, {3, 0}, {-3, -1}, {-3, 1}, {-1, -3}, {-1, 3}, {1, -3}, {1, 3}, {3, -1}, {3, 1}, {-3, -2}, {-3, 2}, {-2, -3}, {-2, 3}, {2, -3}, {2, 3}, {3, -2}, {3, 2}, {-3, -3}, {-3, 3}, {3, -3}, {3, 3}};
+__constant__ int16_t kRowStart[5] = {0, 1, 10, 35, 84};
+
+
 struct GridDev {
     const float4 *sorted;      // sites sorted by grid cell: x, y, z, bits(id)
     const int32_t *cell_start; // [ncell + 1]
@@ -475,13 +481,25 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) cell_kernel(const CellParams
         const int smax = max(P.g.dims[0], max(P.g.dims[1], P.g.dims[2]));
         const float h = P.g.h;
         for (int s = 0; s <= smax && cell.status == kCellOk; ++s) {
-            for (int dz = -s; dz <= s && cell.status == kCellOk; ++dz) {
+            const int npairs = (2 * s + 1) * (2 * s + 1);
+            for (int pi_ = 0; pi_ < npairs && cell.status == kCellOk; ++pi_) {
+                int dz, dy;
+                if (s <= 3) {
+                    // pairs of shells 0..3 in the order of their distance (dz^2 + dy^2)
+                    const int8_t *pr = kRowOrder[kRowStart[s] + pi_];
+                    dz = pr[0];
+                    dy = pr[1];
+                } else {
+                    dz = pi_ / (2 * s + 1) - s;
+                    dy = pi_ % (2 * s + 1) - s;
+                }
+                if (max(abs(dz), abs(dy)) > s) continue;
                 const int z = c[2] + dz;
                 if (z < 0 || z >= P.g.dims[2]) continue;
                 // distance from the site to the slab of cell layer z
                 const float zl = P.g.lo[2] + (float)z * h - p.z, zh = zl + h;
                 const float gz = fmaxf(0.f, fmaxf(zl, -zh));
-                for (int dy = -s; dy <= s && cell.status == kCellOk; ++dy) {
+                {
                     const int y = c[1] + dy;
                     if (y < 0 || y >= P.g.dims[1]) continue;
                     const float yl = P.g.lo[1] + (float)y * h - p.y, yh = yl + h;
