@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s fwd & fwd+bwd at 3M cells vs plain FP32; serving p50/p99 latency"
+RECORD_STEPS = 384  # walk-record steps per ray kept by the training step
 UNIT = "Mrays/s"
 
 
@@ -371,11 +372,13 @@ def mixture_extras(scene, args, dev):
                  pos=torch.zeros(scene.n_sites, 3, device=dev))
     out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
                depth=torch.empty(R, device=dev))
+    tout = dict(out, walk_record=(torch.empty(rf.walk_record_bytes(cams, RECORD_STEPS), dtype=torch.uint8,
+                                              device=dev), RECORD_STEPS))
 
     def step():
-        foam.render(cams, out=out)
-        d, _ = rf.mse_grad(out["rgb"], target, 1.0 / (3 * R))
-        foam.backward(cams, out, d, grads=grads)
+        foam.render(cams, out=tout)
+        d, _ = rf.mse_grad(tout["rgb"], target, 1.0 / (3 * R))
+        foam.backward(cams, tout, d, grads=grads)
 
     for _ in range(2):
         step()
@@ -501,8 +504,12 @@ def main():
     grads = dict(density=torch.zeros(scene.n_sites, device=dev),
                  sh=torch.zeros(scene.n_sites, (deg + 1) ** 2, 3, device=dev),
                  pos=torch.zeros(scene.n_sites, 3, device=dev))
+    # the forward keeps a walk record (which face each step left by) that the
+    # backward replays instead of searching the faces again
     out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
-               depth=torch.empty(R, device=dev))
+               depth=torch.empty(R, device=dev),
+               walk_record=(torch.empty(rf.walk_record_bytes([cam], RECORD_STEPS), dtype=torch.uint8,
+                                        device=dev), RECORD_STEPS))
     loss = torch.zeros(1, device=dev)
     scale = 1.0 / (3 * R)
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -556,15 +563,16 @@ def main():
         ms = float(t.item())
     value = world * R / (ms * 1e-3) / 1e6
 
-    # forward-only throughput
+    # forward-only throughput (rendering alone: no walk record)
     fwd_only = None
     res = {}
+    out_fwd = {k: out[k] for k in ("rgb", "trans", "depth")}
     if not args.no_extras:
         barrier()
         a, b = ev(), ev()
         a.record()
         for _ in range(args.steps):
-            foam.render([cam], out=out)
+            foam.render([cam], out=out_fwd)
         b.record()
         barrier()
         fwd_only = R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
@@ -580,7 +588,7 @@ def main():
             a, b, c = ev(), ev(), ev()
             a.record()
             for _ in range(args.steps):
-                foam.render([cam], out=out)
+                foam.render([cam], out=out_fwd)
             b.record()
             for _ in range(args.steps):
                 step()
@@ -669,7 +677,8 @@ def main():
                                    + (f" (with {scene.n_sites} sites)" if args.sites else ""),
                        "n_sites": scene.n_sites, "n_edges": scene.n_edges, "rays_per_step": R,
                        "cell_steps_per_ray": steps_total / R, "sh_degree": deg,
-                       "step": "fwd + mse grad + bwd (FP32 attributes)",
+                       "step": f"fwd + mse grad + bwd (FP32 attributes; the backward replays a "
+                               f"{RECORD_STEPS}-step walk record of the forward)",
                        "l2": "inputs larger than L2 (packed foam %.2f GB)" % (foam.info()["device_bytes"] / 1e9),
                        "parallelism": f"dp{world}" if world > 1 else "single"},
             "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,

@@ -240,6 +240,15 @@ RF_API rf_status rf_render_bwd(rf_scene *scene, const rf_camera *cams, int32_t n
  *     quantile           optional float [R]
  *     quantile_aux       float [R][5], required with quantile: per-ray sums the
  *                        backward of the quantile loss reads
+ *     walk_record        optional device buffer of walk_record_bytes >=
+ *                        rf_walk_record_bytes(cams, n_cams, walk_record_steps):
+ *                        the forward stores there, for the first
+ *                        walk_record_steps steps of every ray, which face it
+ *                        left each cell by (one byte per step).  Given to
+ *                        rf_render_bwd_ex with the same cameras, options and
+ *                        scene, it lets the backward replay those steps
+ *                        instead of searching the faces again; the gradients
+ *                        are the same bits either way.
  */
 typedef struct rf_fwd_outputs {
     float *rgb;
@@ -249,12 +258,17 @@ typedef struct rf_fwd_outputs {
     uint8_t *ray_status;
     float *quantile;
     float *quantile_aux;
+    uint8_t *walk_record;
+    size_t walk_record_bytes;
+    int32_t walk_record_steps;
 } rf_fwd_outputs;
 
 /*   inputs of rf_render_bwd_ex (device):
  *     rgb, trans, depth      forward outputs (depth may be NULL without d_depth)
  *     quantile_aux           forward output, required with d_quantile
  *     d_rgb                  required; d_trans, d_depth, d_quantile optional
+ *     walk_record            optional: the forward's walk record (same
+ *                            walk_record_bytes and walk_record_steps)
  *   gradients (device, FP32, accumulated +=, each may be NULL):
  *     density [N], sh [N][(deg+1)^2][3], pos [N][3] */
 typedef struct rf_bwd_inputs {
@@ -266,7 +280,14 @@ typedef struct rf_bwd_inputs {
     const float *d_trans;
     const float *d_depth;
     const float *d_quantile;
+    const uint8_t *walk_record;
+    size_t walk_record_bytes;
+    int32_t walk_record_steps;
 } rf_bwd_inputs;
+
+/* Bytes of a walk record of `steps` steps per ray for these cameras (the
+ * rays are grouped by warps of 32 on 16x8 tiles); 0 for bad arguments. */
+RF_API size_t rf_walk_record_bytes(const rf_camera *cams, int32_t n_cams, int32_t steps);
 
 typedef struct rf_grads {
     float *density;

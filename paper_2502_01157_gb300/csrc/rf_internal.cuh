@@ -73,6 +73,8 @@ struct RenderParams {
     float eps;
     int32_t max_steps;
     SphereFx fx;
+    uint8_t *rec;                          // walk record of this launch (warp-major) or null
+    int32_t rec_steps;                     // recorded steps per ray
 };
 
 // ---------------------------------------------------------------------------
@@ -331,7 +333,7 @@ __device__ __forceinline__ void face_test(float x, float y, float z, int slot, c
 }
 
 __device__ __forceinline__ int find_exit(const SceneDev &s, const CellHdr &c, const float3 &d,
-                                         const float3 &oc, float &num_best, float &den_best) {
+                                         const float3 &oc, float &num_best, float &den_best, int &slot) {
     float nb = 1.f, db = 0.f;
     int fb = -1;
     const float4 *f = s.faces + 3 * (size_t)c.gbeg;
@@ -345,7 +347,27 @@ __device__ __forceinline__ int find_exit(const SceneDev &s, const CellHdr &c, co
     }
     num_best = nb;
     den_best = db;
+    slot = fb;
     return fb >= 0 ? ldg(s.nbr + 4 * (size_t)c.gbeg + fb) : -1;
+}
+
+// Walk record: the forward stores, per ray step, the slot of the exit face it
+// found (one byte); the backward replays that face instead of testing them
+// all, with the same arithmetic as face_test, so it gets the same exit.
+constexpr int kRecSearch = 0xFE;  // not recorded (slot too large): search again
+constexpr int kRecNoExit = 0xFF;  // the cell had no exit
+
+__device__ __forceinline__ int exit_of_slot(const SceneDev &s, const CellHdr &c, const float3 &d,
+                                            const float3 &oc, int slot, float &nb, float &db) {
+    const float4 *f = s.faces + 3 * ((size_t)c.gbeg + (slot >> 2));
+    const float4 X = ldg(f), Y = ldg(f + 1), Z = ldg(f + 2);
+    const int e = slot & 3;
+    const float x = e == 0 ? X.x : e == 1 ? X.y : e == 2 ? X.z : X.w;
+    const float y = e == 0 ? Y.x : e == 1 ? Y.y : e == 2 ? Y.z : Y.w;
+    const float z = e == 0 ? Z.x : e == 1 ? Z.y : e == 2 ? Z.z : Z.w;
+    db = __fmaf_rn(x, d.x, __fmaf_rn(y, d.y, __fmul_rn(z, d.z)));
+    nb = __fmaf_rn(-x, oc.x, __fmaf_rn(-y, oc.y, __fmaf_rn(-z, oc.z, 1.f)));
+    return ldg(s.nbr + 4 * (size_t)c.gbeg + slot);
 }
 
 // One segment's bounds, width, density and colour (shared by all kernels).
@@ -363,14 +385,24 @@ struct Segment {
 // With FX, ts is the current ray's next sphere crossing (+inf: none): when it
 // falls in [t0, t1) and before t_max the segment ends there instead of at the
 // face.
+// replay >= 0: the walk record's code for this step (the exit slot, or
+// kRecNoExit); otherwise the faces are searched and *code (if given) receives
+// the record code of the exit found.
 template <typename AT, int DEG, bool FX = false>
 __device__ __forceinline__ void cell_step(const SceneDev &s, int i, const CellHdr &cell,
                                           const float3 &o, const float3 &d, float t0, float tmin,
                                           float tmax, const float *Y, Segment &g, float3 &oc,
-                                          float ts = 0.f) {
+                                          float ts = 0.f, int replay = -1, int *code = nullptr) {
     oc = make_float3(__fsub_rn(o.x, cell.x), __fsub_rn(o.y, cell.y), __fsub_rn(o.z, cell.z));
-    float nb, db;
-    g.next = find_exit(s, cell, d, oc, nb, db);
+    float nb = 1.f, db = 0.f;
+    // a slot beyond the cell's faces (a record of another scene) is searched
+    if (replay >= 0 && replay != kRecSearch && (replay == kRecNoExit || replay < 4 * cell.gcnt)) {
+        g.next = replay == kRecNoExit ? -1 : exit_of_slot(s, cell, d, oc, replay, nb, db);
+    } else {
+        int slot;
+        g.next = find_exit(s, cell, d, oc, nb, db, slot);
+        if (code) *code = g.next < 0 ? kRecNoExit : slot < kRecSearch ? slot : kRecSearch;
+    }
     g.t1 = g.next >= 0 ? __fdiv_rn(nb, db) : __int_as_float(0x7f800000);
     g.a = t0 > tmin ? t0 : tmin;
     float tend = g.t1;
@@ -486,7 +518,8 @@ __device__ __forceinline__ int locate_from(const SceneDev &s, int i, const float
         const CellHdr cell = load_cell(s, i);
         const float3 oc = make_float3(__fsub_rn(c.x, cell.x), __fsub_rn(c.y, cell.y), __fsub_rn(c.z, cell.z));
         float nb, db;
-        const int nx = find_exit(s, cell, d, oc, nb, db);
+        int slot;
+        const int nx = find_exit(s, cell, d, oc, nb, db, slot);
         if (nx < 0 || !(__fdiv_rn(nb, db) < L)) break;
         i = nx;
     }

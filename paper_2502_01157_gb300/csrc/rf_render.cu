@@ -1,6 +1,7 @@
 // rf_render.cu -- C-ABI entry points of the Radiant Foam renderer (arXiv
 // 2502.01157): forward, backward and trace over a packed scene, and the
 // kernels of rf_kernels.cuh instantiated without the sphere effect.
+#include <algorithm>
 #include <cstring>
 
 #include "rf_kernels.cuh"
@@ -51,6 +52,24 @@ __global__ void mse_grad_kernel(const float *__restrict__ rgb, const float *__re
 // Host side
 // ---------------------------------------------------------------------------
 
+// Walk-record bytes of the launch holding cams[first .. first + count).
+static size_t record_bytes_of(const rf_camera *cams, int first, int count, int32_t steps) {
+    int64_t tiles = 0;
+    for (int c = first; c < first + count; ++c)
+        tiles += (int64_t)((cams[c].width + kTileW - 1) / kTileW) * ((cams[c].height + kTileH - 1) / kTileH);
+    return (size_t)tiles * (kBlock / 32) * (size_t)steps * 32;
+}
+
+static rf_status check_record(const rf_camera *cams, int32_t n_cams, const void *rec, size_t bytes, int32_t steps) {
+    if (!rec) return RF_OK;
+    if (steps < 1 || steps > (1 << 20)) return fail(RF_ERR_INVALID_ARG, "walk_record_steps must be in [1, 2^20]");
+    size_t need = 0;
+    for (int first = 0; first < n_cams; first += kMaxCamsPerLaunch)
+        need += record_bytes_of(cams, first, std::min(n_cams - first, kMaxCamsPerLaunch), steps);
+    if (bytes < need) return fail(RF_ERR_INVALID_ARG, "walk_record holds %zu bytes, needs %zu", bytes, need);
+    return RF_OK;
+}
+
 static rf_status common_checks(const rf_scene *s, const rf_camera *cams, int32_t n_cams,
                                const rf_render_opts *opts, float *eps, int32_t *max_steps,
                                SphereFx *fx) {
@@ -93,7 +112,8 @@ rf_status launch_fwd_batch(const rf_scene *s, const rf_camera *cams, const int64
 using namespace rf;
 
 static rf_status render_fwd_impl(rf_scene *s, const rf_camera *cams, int32_t n_cams,
-                                 const rf_render_opts *opts, FwdOut out, int mode, void *stream) {
+                                 const rf_render_opts *opts, FwdOut out, int mode, void *stream,
+                                 uint8_t *rec = nullptr, size_t rec_bytes = 0, int32_t rec_steps = 0) {
     float eps;
     int32_t max_steps;
     SphereFx fx;
@@ -107,7 +127,10 @@ static rf_status render_fwd_impl(rf_scene *s, const rf_camera *cams, int32_t n_c
     p.eps = eps;
     p.max_steps = max_steps;
     p.fx = fx;
+    if ((rc = check_record(cams, n_cams, rec, rec_bytes, rec_steps)) != RF_OK) return rc;
+    p.rec_steps = rec_steps;
     int64_t ray_begin = 0;
+    size_t rec_off = 0;
     for (int first = 0; first < n_cams; first += kMaxCamsPerLaunch) {
         const int count = n_cams - first < kMaxCamsPerLaunch ? n_cams - first : kMaxCamsPerLaunch;
         rc = launch_nearest_sites(s, cams + first, count, s->start_keys, st);
@@ -115,6 +138,8 @@ static rf_status render_fwd_impl(rf_scene *s, const rf_camera *cams, int32_t n_c
         const int64_t tiles = make_launch_cams(cams, first, count, ray_begin, &p.lc);
         if (tiles >= (1ll << 31)) return fail(RF_ERR_INVALID_ARG, "too many tiles in one launch");
         for (int c = 0; c < count; ++c) ray_begin += (int64_t)cams[first + c].width * cams[first + c].height;
+        p.rec = rec ? rec + rec_off : nullptr;
+        if (rec) rec_off += record_bytes_of(cams, first, count, rec_steps);
         launch_fwd_fx(p, s->attr_dtype, s->sh_degree, mode, tiles, out, st);
         RF_CUDA(cudaGetLastError());
     }
@@ -129,13 +154,14 @@ RF_API rf_status rf_render_fwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_
         return fail(RF_ERR_INVALID_ARG, "quantile_aux is required with quantile");
     FwdOut out = {o->rgb, o->trans, o->depth, o->steps, o->ray_status, nullptr, 0, o->quantile,
                   o->quantile_aux};
-    return render_fwd_impl(s, cams, n_cams, opts, out, o->quantile ? kQuant : kPlain, stream);
+    return render_fwd_impl(s, cams, n_cams, opts, out, o->quantile ? kQuant : kPlain, stream, o->walk_record,
+                           o->walk_record_bytes, o->walk_record_steps);
 }
 
 RF_API rf_status rf_render_fwd(rf_scene *s, const rf_camera *cams, int32_t n_cams,
                                const rf_render_opts *opts, float *rgb, float *trans, float *depth,
                                int32_t *steps, uint8_t *ray_status, void *stream) {
-    const rf_fwd_outputs o = {rgb, trans, depth, steps, ray_status, nullptr, nullptr};
+    const rf_fwd_outputs o = {rgb, trans, depth, steps, ray_status, nullptr, nullptr, nullptr, 0, 0};
     return rf_render_fwd_ex(s, cams, n_cams, opts, &o, stream);
 }
 
@@ -173,7 +199,11 @@ RF_API rf_status rf_render_bwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_
     p.eps = eps;
     p.max_steps = max_steps;
     p.fx = fx;
+    if ((rc = check_record(cams, n_cams, in->walk_record, in->walk_record_bytes, in->walk_record_steps)) != RF_OK)
+        return rc;
+    p.rec_steps = in->walk_record_steps;
     int64_t ray_begin = 0;
+    size_t rec_off = 0;
     for (int first = 0; first < n_cams; first += kMaxCamsPerLaunch) {
         const int count = n_cams - first < kMaxCamsPerLaunch ? n_cams - first : kMaxCamsPerLaunch;
         rc = launch_nearest_sites(s, cams + first, count, s->start_keys, st);
@@ -181,6 +211,8 @@ RF_API rf_status rf_render_bwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_
         const int64_t tiles = make_launch_cams(cams, first, count, ray_begin, &p.lc);
         if (tiles >= (1ll << 31)) return fail(RF_ERR_INVALID_ARG, "too many tiles in one launch");
         for (int c = 0; c < count; ++c) ray_begin += (int64_t)cams[first + c].width * cams[first + c].height;
+        p.rec = in->walk_record ? const_cast<uint8_t *>(in->walk_record) + rec_off : nullptr;
+        if (in->walk_record) rec_off += record_bytes_of(cams, first, count, in->walk_record_steps);
         launch_bwd_fx(p, s->attr_dtype, s->sh_degree, quant, tiles, io, st);
         RF_CUDA(cudaGetLastError());
     }
@@ -192,7 +224,7 @@ RF_API rf_status rf_render_bwd(rf_scene *s, const rf_camera *cams, int32_t n_cam
                                const float *depth, const float *d_rgb, const float *d_trans,
                                const float *d_depth, float *g_density, float *g_sh, float *g_pos,
                                void *stream) {
-    const rf_bwd_inputs in = {rgb, trans, depth, nullptr, d_rgb, d_trans, d_depth, nullptr};
+    const rf_bwd_inputs in = {rgb, trans, depth, nullptr, d_rgb, d_trans, d_depth, nullptr, nullptr, 0, 0};
     const rf_grads gr = {g_density, g_sh, g_pos};
     return rf_render_bwd_ex(s, cams, n_cams, opts, &in, &gr, stream);
 }
@@ -206,4 +238,12 @@ RF_API rf_status rf_mse_grad(const float *rgb, const float *target, int64_t n, f
     mse_grad_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(rgb, target, n, scale, d_rgb, loss);
     RF_CUDA(cudaGetLastError());
     return RF_OK;
+}
+
+RF_API size_t rf_walk_record_bytes(const rf_camera *cams, int32_t n_cams, int32_t steps) {
+    if (!cams || n_cams < 1 || steps < 1) return 0;
+    size_t need = 0;
+    for (int first = 0; first < n_cams; first += kMaxCamsPerLaunch)
+        need += record_bytes_of(cams, first, std::min(n_cams - first, kMaxCamsPerLaunch), steps);
+    return need;
 }

@@ -73,14 +73,17 @@ class rf_serve_metrics(ctypes.Structure):
 class rf_fwd_outputs(ctypes.Structure):
     _fields_ = [("rgb", ctypes.c_void_p), ("trans", ctypes.c_void_p), ("depth", ctypes.c_void_p),
                 ("steps", ctypes.c_void_p), ("ray_status", ctypes.c_void_p),
-                ("quantile", ctypes.c_void_p), ("quantile_aux", ctypes.c_void_p)]
+                ("quantile", ctypes.c_void_p), ("quantile_aux", ctypes.c_void_p),
+                ("walk_record", ctypes.c_void_p), ("walk_record_bytes", ctypes.c_size_t),
+                ("walk_record_steps", ctypes.c_int32)]
 
 
 class rf_bwd_inputs(ctypes.Structure):
     _fields_ = [("rgb", ctypes.c_void_p), ("trans", ctypes.c_void_p), ("depth", ctypes.c_void_p),
                 ("quantile_aux", ctypes.c_void_p), ("d_rgb", ctypes.c_void_p),
                 ("d_trans", ctypes.c_void_p), ("d_depth", ctypes.c_void_p),
-                ("d_quantile", ctypes.c_void_p)]
+                ("d_quantile", ctypes.c_void_p), ("walk_record", ctypes.c_void_p),
+                ("walk_record_bytes", ctypes.c_size_t), ("walk_record_steps", ctypes.c_int32)]
 
 
 class rf_grads(ctypes.Structure):
@@ -129,6 +132,7 @@ SIGNATURES = {
     "rf_trace_cells": (_S, [_P, ctypes.POINTER(rf_camera), ctypes.POINTER(rf_render_opts),
                             ctypes.c_int32, _P, _P, _P]),
     "rf_mse_grad": (_S, [_P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
+    "rf_walk_record_bytes": (ctypes.c_size_t, [ctypes.POINTER(rf_camera), ctypes.c_int32, ctypes.c_int32]),
     "rf_adjacency_create": (_S, [ctypes.POINTER(_P)]),
     "rf_adjacency_build": (_S, [_P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                 _P]),
@@ -222,6 +226,12 @@ def camera_array(cams) -> "ctypes.Array":
     for k, c in enumerate(cams):
         arr[k] = camera_struct(c)
     return arr
+
+
+def walk_record_bytes(cams, steps: int) -> int:
+    """Bytes of a walk record of ``steps`` steps per ray for ``cams``."""
+    ca = camera_array(cams)
+    return int(lib().rf_walk_record_bytes(ca, len(ca), int(steps)))
 
 
 def opts_struct(eps: float = 1e-4, max_steps: int = 0, effects=None) -> rf_render_opts:
@@ -343,11 +353,13 @@ class Foam:
 
     def render(self, cams, eps: float = 1e-4, max_steps: int = 0, steps: bool = False,
                status: bool = False, quantile: bool = False, out=None, stream=None,
-               effects=None) -> dict:
+               effects=None, record: int = 0) -> dict:
         """Forward render; returns rgb [R,3], trans [R], depth [R] (+ steps,
         status; + quantile [R] and quantile_aux [R,5] with ``quantile``) as
         CUDA tensors, rays of the cameras concatenated.  ``effects``: an
-        analytic sphere the rays reflect off or refract through."""
+        analytic sphere the rays reflect off or refract through.  ``record``
+        > 0: also keep a walk record of that many steps per ray
+        (``out["walk_record"]``), which lets :meth:`backward` replay the walk."""
         ca = camera_array(cams)
         R = n_rays_of(cams)
         dev = self.pos.device
@@ -361,10 +373,17 @@ class Foam:
             if quantile:
                 out["quantile"] = torch.empty(R, device=dev)
                 out["quantile_aux"] = torch.empty(R, 5, device=dev)
+            if record:
+                out["walk_record"] = (torch.empty(walk_record_bytes(cams, record), dtype=torch.uint8,
+                                                  device=dev), int(record))
         o = opts_struct(eps, max_steps, effects)
+        rec = out.get("walk_record")
         fo = rf_fwd_outputs(_addr(out["rgb"]), _addr(out["trans"]), _addr(out["depth"]),
                             _addr(out.get("steps")), _addr(out.get("status")),
-                            _addr(out.get("quantile")), _addr(out.get("quantile_aux")))
+                            _addr(out.get("quantile")), _addr(out.get("quantile_aux")),
+                            _addr(rec[0]) if rec is not None else None,
+                            rec[0].numel() if rec is not None else 0,
+                            rec[1] if rec is not None else 0)
         _check(lib().rf_render_fwd_ex(self.handle, ca, len(ca), ctypes.byref(o), ctypes.byref(fo),
                                       _stream(stream)))
         return out
@@ -382,9 +401,13 @@ class Foam:
                          pos=torch.zeros(self.n_sites, 3, device=dev))
         ca = camera_array(cams)
         o = opts_struct(eps, max_steps, effects)
+        rec = fwd.get("walk_record")
         bi = rf_bwd_inputs(_addr(fwd["rgb"]), _addr(fwd["trans"]), _addr(fwd.get("depth")),
                            _addr(fwd.get("quantile_aux")), _addr(d_rgb), _addr(d_trans),
-                           _addr(d_depth), _addr(d_quantile))
+                           _addr(d_depth), _addr(d_quantile),
+                           _addr(rec[0]) if rec is not None else None,
+                           rec[0].numel() if rec is not None else 0,
+                           rec[1] if rec is not None else 0)
         go = rf_grads(_addr(grads.get("density")), _addr(grads.get("sh")), _addr(grads.get("pos")))
         _check(lib().rf_render_bwd_ex(self.handle, ca, len(ca), ctypes.byref(o), ctypes.byref(bi),
                                       ctypes.byref(go), _stream(stream)))
@@ -520,9 +543,11 @@ def render_noalloc(pos, adj_off, adj_idx, density, sh, aabb, cams, eps: float = 
 
 class _Render(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, foam, cams, eps, max_steps, quantile, effects, density, sh, pos):
+    def forward(ctx, foam, cams, eps, max_steps, quantile, effects, record, density, sh, pos):
         foam._sync_positions(pos)
-        out = foam.render(cams, eps=eps, max_steps=max_steps, quantile=quantile, effects=effects)
+        out = foam.render(cams, eps=eps, max_steps=max_steps, quantile=quantile, effects=effects,
+                          record=record)
+        ctx.walk_record = out.get("walk_record")
         ctx.foam, ctx.cams, ctx.eps, ctx.max_steps, ctx.quantile = foam, cams, eps, max_steps, quantile
         ctx.effects = effects
         ctx.dtypes = (density.dtype, sh.dtype)
@@ -540,17 +565,19 @@ class _Render(torch.autograd.Function):
         need = ctx.needs_input_grad
         dev = rgb.device
         grads = {}
-        if need[6]:
-            grads["density"] = torch.zeros(foam.n_sites, device=dev)
         if need[7]:
-            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+            grads["density"] = torch.zeros(foam.n_sites, device=dev)
         if need[8]:
+            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+        if need[9]:
             grads["pos"] = torch.zeros(foam.n_sites, 3, device=dev)
         if grads:
             z = lambda g: None if g is None else g.contiguous().float()
             fwd = dict(rgb=rgb, trans=trans, depth=depth)
             if ctx.quantile:
                 fwd["quantile_aux"] = saved[3]
+            if ctx.walk_record is not None:
+                fwd["walk_record"] = ctx.walk_record
             foam.backward(ctx.cams, fwd,
                           z(g_rgb) if g_rgb is not None else torch.zeros_like(rgb),
                           z(g_trans), z(g_depth), grads=grads, eps=ctx.eps,
@@ -558,22 +585,25 @@ class _Render(torch.autograd.Function):
                           effects=ctx.effects)
         gd = grads.get("density")
         gs = grads.get("sh")
-        return (None, None, None, None, None, None,
+        ctx.walk_record = None
+        return (None, None, None, None, None, None, None,
                 None if gd is None else gd.to(ctx.dtypes[0]),
                 None if gs is None else gs.to(ctx.dtypes[1]),
                 grads.get("pos"))
 
 
 def render(foam: Foam, cams, density=None, sh=None, pos=None, eps: float = 1e-4,
-           max_steps: int = 0, quantile: bool = False, effects=None):
+           max_steps: int = 0, quantile: bool = False, effects=None, record: int = 256):
     """Differentiable render of ``cams``: returns (rgb [R,3], trans [R],
     depth [R]) and, with ``quantile``, the per-ray quantile loss of Eq. (6)
     [R]; gradients flow to ``density``, ``sh`` and ``pos`` (defaults: the
-    foam's own tensors).  A changed ``pos`` is re-packed first."""
+    foam's own tensors).  A changed ``pos`` is re-packed first.  ``record``:
+    steps per ray of the walk record kept between the passes (0: none; the
+    backward then searches every step's exit again)."""
     density = foam.density if density is None else density
     sh = foam.sh if sh is None else sh
     if density is not foam.density or sh is not foam.sh:
         foam.set_attributes(density.detach(), sh.detach())
     if pos is None:
         pos = foam.pos
-    return _Render.apply(foam, cams, eps, max_steps, bool(quantile), effects, density, sh, pos)
+    return _Render.apply(foam, cams, eps, max_steps, bool(quantile), effects, int(record), density, sh, pos)
