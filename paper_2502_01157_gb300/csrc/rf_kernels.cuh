@@ -431,17 +431,27 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                 }
             }
             __syncwarp();
-            const int c0 = lane, c1 = lane + 32;  // the two value columns this lane sums
+            // 16-byte columns: lanes 0..15 sum the first group of a pass,
+            // lanes 16..31 the second; a lane sums four values at once and
+            // adds them with one vector atomic where they are four SH values
+            constexpr int NQ = VP / 4;
+            constexpr int SQ = SP / 4;
+            const float4 *stage4 = reinterpret_cast<const float4 *>(stage);
+            const int hl = lane & 15;
             while (leaders) {
-                const int L = __ffs(leaders) - 1;
+                const int L0 = __ffs(leaders) - 1;
                 leaders &= leaders - 1;
+                const bool two = leaders != 0;
+                const int L1 = two ? __ffs(leaders) - 1 : L0;
+                if (two) leaders &= leaders - 1;
+                const int L = lane >= 16 ? L1 : L0;
                 const unsigned m = __shfl_sync(full, peers, L);
                 const int cell_i = __shfl_sync(full, i, L);
                 const int cell_a = __shfl_sync(full, key_prev, L);
-                float s0 = 0.f, s1 = 0.f;
-                if (c0 < V) {  // a lane only reads the columns that exist (V may be < 32)
+                if ((lane < 16 || two) && hl < NQ) {
                     // four members per pass with independent loads; an absent
                     // member reads the zero row 32
+                    float4 sm = make_float4(0.f, 0.f, 0.f, 0.f);
                     for (unsigned mm = m; mm;) {
                         const int k0 = __ffs(mm) - 1;
                         mm &= mm - 1;
@@ -451,22 +461,30 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                         mm &= mm - 1;
                         const int k3 = mm ? __ffs(mm) - 1 : 32;
                         mm &= mm - 1;
-                        s0 += (stage[k0 * SP + c0] + stage[k1 * SP + c0]) +
-                              (stage[k2 * SP + c0] + stage[k3 * SP + c0]);
-                        if (c1 < V)
-                            s1 += (stage[k0 * SP + c1] + stage[k1 * SP + c1]) +
-                                  (stage[k2 * SP + c1] + stage[k3 * SP + c1]);
+                        const float4 a0 = stage4[k0 * SQ + hl], a1 = stage4[k1 * SQ + hl];
+                        const float4 a2 = stage4[k2 * SQ + hl], a3 = stage4[k3 * SQ + hl];
+                        sm.x += (a0.x + a1.x) + (a2.x + a3.x);
+                        sm.y += (a0.y + a1.y) + (a2.y + a3.y);
+                        sm.z += (a0.z + a1.z) + (a2.z + a3.z);
+                        sm.w += (a0.w + a1.w) + (a2.w + a3.w);
                     }
-                }
+                    const int c = 4 * hl;
+                    const bool nz = sm.x != 0.f || sm.y != 0.f || sm.z != 0.f || sm.w != 0.f;
+                    if (NV % 4 == 0 && c + 3 < NV && io.sh_vec) {
+                        if (nz) atomicAdd(reinterpret_cast<float4 *>(io.g_sh + (size_t)cell_i * NV + c), sm);
+                    } else if (nz) {
+                        const float v4[4] = {sm.x, sm.y, sm.z, sm.w};
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int col = h ? c1 : c0;
-                    const float sum = h ? s1 : s0;
-                    if (col < V && sum != 0.f) {
-                        if (col < NV) atomicAdd(io.g_sh + (size_t)cell_i * NV + col, sum);
-                        else if (col == NV) atomicAdd(io.g_density + cell_i, sum);
-                        else if (col < NV + 4) atomicAdd(io.g_pos + 3 * (int64_t)cell_i + (col - NV - 1), sum);
-                        else if (cell_a >= 0) atomicAdd(io.g_pos + 3 * (int64_t)cell_a + (col - NV - 4), sum);
+                        for (int j = 0; j < 4; ++j) {
+                            const int col = c + j;
+                            const float sum = v4[j];
+                            if (col < V && sum != 0.f) {
+                                if (col < NV) atomicAdd(io.g_sh + (size_t)cell_i * NV + col, sum);
+                                else if (col == NV) atomicAdd(io.g_density + cell_i, sum);
+                                else if (col < NV + 4) atomicAdd(io.g_pos + 3 * (int64_t)cell_i + (col - NV - 1), sum);
+                                else if (cell_a >= 0) atomicAdd(io.g_pos + 3 * (int64_t)cell_a + (col - NV - 4), sum);
+                            }
+                        }
                     }
                 }
             }
