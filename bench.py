@@ -81,6 +81,13 @@ def bytes_per_step(k_bar, deg, attr_bytes):
     return 16 + 12 * k_bar + 4 + attr_bytes + 3 * (deg + 1) ** 2 * attr_bytes
 
 
+def replay_bytes_per_step(deg, attr_bytes):
+    """Algorithmic bytes one replayed backward step reads (no reuse): the
+    walk-record byte, cell header 16 B, the exit face 12 B, its neighbour id
+    4 B, density and SH coefficients."""
+    return 1 + 16 + 12 + 4 + attr_bytes + 3 * (deg + 1) ** 2 * attr_bytes
+
+
 def bwd_extra_bytes_per_step(deg):
     """Backward: read-modify-write of the FP32 gradients touched per step:
     density 4 B, SH 12 (deg+1)^2 B, and two site positions (one crossing) 24 B."""
@@ -645,10 +652,14 @@ def main():
     e2e_s = (time.perf_counter() - w0) / args.steps
     barrier()
 
-    # roofline of the dominant kernel (the backward re-walk)
+    # roofline of the dominant kernel (the backward, replaying the walk record
+    # for the first RECORD_STEPS steps of every ray and searching after them)
     attr_b = 4
-    fwd_bytes = bytes_per_step(k_bar, deg, attr_b) * steps_total + 20 * R
-    bwd_bytes = (bytes_per_step(k_bar, deg, attr_b) + bwd_extra_bytes_per_step(deg)) * steps_total + 32 * R
+    fwd_bytes = (bytes_per_step(k_bar, deg, attr_b) + 1) * steps_total + 20 * R
+    steps_replayed = int(chk["steps"].clamp(max=RECORD_STEPS).sum().item())
+    bwd_step_bytes = (replay_bytes_per_step(deg, attr_b) * steps_replayed
+                      + bytes_per_step(k_bar, deg, attr_b) * (steps_total - steps_replayed)) / steps_total
+    bwd_bytes = (bwd_step_bytes + bwd_extra_bytes_per_step(deg)) * steps_total + 32 * R
     import json as _j
 
     peaks = {}
@@ -666,8 +677,10 @@ def main():
             "traffic": measured_traffic(f"{dominant}_kernel<float,{deg}>", args.workload if not args.sites else f"{args.workload}@{scene.n_sites}"),
             "algorithmic_bytes_per_launch": kb, "kernel_source": kernel_source_hash(),
             "note": "algorithmic bytes are served >99% by L1/L2 (traffic = ncu DRAM bytes per "
-                    "launch); the binding unit is the L1 load data path, see profiles/", "bytes_per_cell_step": (bytes_per_step(k_bar, deg, attr_b) +
-                                                     (bwd_extra_bytes_per_step(deg) if dominant == "bwd" else 0)),
+                    "launch); the binding unit is the L1 load data path, see profiles/",
+            "bytes_per_cell_step": (bwd_step_bytes + bwd_extra_bytes_per_step(deg) if dominant == "bwd"
+                                    else bytes_per_step(k_bar, deg, attr_b) + 1),
+            "steps_replayed_frac": steps_replayed / steps_total,
             "cell_steps_per_launch": steps_total, "ms_per_launch": kms}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
