@@ -11,9 +11,10 @@
 // along its boundary cycle.  Candidates come from a uniform grid, shell by
 // shell around the site's grid cell, nearest first inside each batch of 32.
 // A site k can cut the cell only if |p_k - p_i| < 2 R, R the cell's largest
-// vertex distance, so the search stops once every site closer than 2 R has
-// been seen (the security radius).  The neighbours are the sites whose planes
-// still hold a vertex at the end.
+// vertex distance (rows of the grid beyond that are skipped), and only if it
+// lies in the ball about some vertex v of radius |v|; the search stops once
+// all those balls lie in the scanned block of grid cells.  The neighbours are
+// the sites whose planes still hold a vertex at the end.
 //
 // The inside/outside test of a vertex is made in FP32 with an error bound;
 // when the FP32 value lies within the bound, the vertex and the test are
@@ -41,9 +42,23 @@ enum : int32_t { kCellOk = 0, kCellOverflow = 1, kCellBroken = 2 };
 
 // The (dz, dy) rows of the blocks of shells 0..3 sorted by dz^2 + dy^2 (then
 // dz, dy): nearer rows first, so the first cuts come from nearer sites.
-__constant__ int8_t kRowOrder[84][2] = {{0, 0}, {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}, {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}, {-2, 0}, {0, -2}, {0, 2}, {2, 0}, {-2, -1}, {-2, 1}, {-1, -2}, {-1, 2}, {1, -2}, {1, 2}, {2, -1}, {2, 1}, {-2, -2}, {-2, 2}, {2, -2}, {2, 2}, {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}, {-2, 0}, {0, -2}, {0, 2}, {2, 0}, {-2, -1}, {-2, 1}, {-1, -2}, {-1, 2}, {1, -2}, {1, 2}, {2, -1}, {2, 1}, {-2, -2}, {-2, 2}, {2, -2}, {2, 2}, {-3, 0}, {0, -3}, {0, 3}, {3, 0}, {-3, -1}, {-3, 1}, {-1, -3}, {-1, 3}, {1, -3}, {1, 3}, {3, -1}, {3, 1}, {-3, -2}, {-3, 2}, {-2, -3}, {-2, 3}, {2, -3}, {2, 3}, {3, -2}, {3, 2}, {-3, -3}, {-3, 3}, {3, -3}, {3, 3}};
+__constant__ int8_t kRowOrder[84][2] = {
+    // shell 0: the 1 rows of its 1x1 block
+    {0, 0},
+    // shell 1: the 9 rows of its 3x3 block
+    {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1},
+    // shell 2: the 25 rows of its 5x5 block
+    {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}, {-2, 0},
+    {0, -2}, {0, 2}, {2, 0}, {-2, -1}, {-2, 1}, {-1, -2}, {-1, 2}, {1, -2}, {1, 2}, {2, -1},
+    {2, 1}, {-2, -2}, {-2, 2}, {2, -2}, {2, 2},
+    // shell 3: the 49 rows of its 7x7 block
+    {0, 0}, {-1, 0}, {0, -1}, {0, 1}, {1, 0}, {-1, -1}, {-1, 1}, {1, -1}, {1, 1}, {-2, 0},
+    {0, -2}, {0, 2}, {2, 0}, {-2, -1}, {-2, 1}, {-1, -2}, {-1, 2}, {1, -2}, {1, 2}, {2, -1},
+    {2, 1}, {-2, -2}, {-2, 2}, {2, -2}, {2, 2}, {-3, 0}, {0, -3}, {0, 3}, {3, 0}, {-3, -1},
+    {-3, 1}, {-1, -3}, {-1, 3}, {1, -3}, {1, 3}, {3, -1}, {3, 1}, {-3, -2}, {-3, 2}, {-2, -3},
+    {-2, 3}, {2, -3}, {2, 3}, {3, -2}, {3, 2}, {-3, -3}, {-3, 3}, {3, -3}, {3, 3}
+};
 __constant__ int16_t kRowStart[5] = {0, 1, 10, 35, 84};
-
 
 struct GridDev {
     const float4 *sorted;      // sites sorted by grid cell: x, y, z, bits(id)
