@@ -94,6 +94,7 @@ struct CellSmem {
     uint32_t ebits[MAXP * (MAXP / 32)];  // directed edges of the removed triangles
     uint32_t src_seen[MAXP / 32];        // boundary-edge sources seen in this cut
     float vlen[2 * MAXP];                // |vertex|
+    float box[6];                        // bounding box of the vertices (with their error bounds)
     uint8_t nxt[MAXP];                   // boundary cycle: a -> nxt[a]
     uint8_t cyc[MAXP];
 };
@@ -178,11 +179,50 @@ struct Cell {
     __device__ Cell(CellSmem<MAXP> &sm, const CellParams &p, int l, const double *pi64)
         : m(sm), P(p), lane(l), pi(pi64) {}
 
-    __device__ void update_radius() {
+    // signed floats as ints of the same order, for the warp min / max reductions
+    static __device__ __forceinline__ int okey(float f) {
+        const int b = __float_as_int(f);
+        return b >= 0 ? b : b ^ 0x7fffffff;
+    }
+    static __device__ __forceinline__ float okey_inv(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+    // radius and bounding box of the current vertices
+    __device__ void update_bounds() {
         float r = 0.f;
-        for (int t = lane; t < n_tri; t += 32) r = fmaxf(r, m.vlen[t] + m.vtx[t].w);
+        int lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+        for (int t = lane; t < n_tri; t += 32) {
+            const float4 v = m.vtx[t];
+            r = fmaxf(r, m.vlen[t] + v.w);
+            lo[0] = min(lo[0], okey(v.x - v.w));
+            lo[1] = min(lo[1], okey(v.y - v.w));
+            lo[2] = min(lo[2], okey(v.z - v.w));
+            hi[0] = max(hi[0], okey(v.x + v.w));
+            hi[1] = max(hi[1], okey(v.y + v.w));
+            hi[2] = max(hi[2], okey(v.z + v.w));
+        }
         r = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r)));  // r >= 0
         R2 = r * r * (1.f + 1e-5f);
+        for (int a = 0; a < 3; ++a) {
+            const float l = okey_inv(__reduce_min_sync(0xffffffffu, lo[a]));
+            const float h = okey_inv(__reduce_max_sync(0xffffffffu, hi[a]));
+            if (lane == 0) {
+                m.box[a] = l;
+                m.box[3 + a] = h;
+            }
+        }
+        __syncwarp();
+    }
+
+    // Can the bisector of a site at d reach the cell?  Its half-space n . x <=
+    // |n|^2 / 2 (n = d) holds the whole bounding box when the box's support in
+    // direction n is below |n|^2 / 2; with a margin for the FP32 rounding, a
+    // "no" is certain.
+    __device__ __forceinline__ bool may_cut(const float3 &d, float d2) const {
+        const float sx = d.x * m.box[d.x > 0.f ? 3 : 0];
+        const float sy = d.y * m.box[d.y > 0.f ? 4 : 1];
+        const float sz = d.z * m.box[d.z > 0.f ? 5 : 2];
+        const float mag = fabsf(sx) + fabsf(sy) + fabsf(sz) + 0.5f * d2;
+        return sx + sy + sz > 0.5f * d2 - 1e-5f * mag;
     }
 
     __device__ __forceinline__ void put_vertex(int t, const float4 &v) {
@@ -221,7 +261,7 @@ struct Cell {
         }
         n_tri = 8;
         __syncwarp();
-        update_radius();
+        update_bounds();
     }
 
     __device__ int alloc_slot() {
@@ -396,20 +436,17 @@ struct Cell {
         //    and the new radius
         uint32_t used[PW];
         for (int w = 0; w < PW; ++w) used[w] = 0u;
-        float r = 0.f;
         for (int t = lane; t < n_tri; t += 32) {
             const uint32_t tv = m.tri[t];
             const uint32_t e[3] = {tv & 255, (tv >> 8) & 255, (tv >> 16) & 255};
 #pragma unroll
             for (int j = 0; j < 3; ++j) used[e[j] >> 5] |= 1u << (e[j] & 31);
-            r = fmaxf(r, m.vlen[t] + m.vtx[t].w);
         }
         for (int w = 0; w < PW; ++w) {
             used[w] = __reduce_or_sync(full, used[w]);
             if (!((used[w] >> lane) & 1u)) m.pid[w * 32 + lane] = kFreeSlot;
         }
-        r = __uint_as_float(__reduce_max_sync(full, __float_as_uint(r)));
-        R2 = r * r * (1.f + 1e-5f);
+        update_bounds();
         __syncwarp();
     }
 
@@ -443,7 +480,7 @@ struct Cell {
     // Offer one candidate per lane; cut by the qualifying ones nearest first.
     __device__ void offer(bool valid, int32_t k, const float3 &d, float d2, bool check_dup) {
         const unsigned full = 0xffffffffu;
-        valid = valid && d2 > 0.f && d2 < 4.f * R2;
+        valid = valid && d2 > 0.f && d2 < 4.f * R2 && may_cut(d, d2);
         while (status == kCellOk) {
             const unsigned v = __ballot_sync(full, valid);
             if (!v) break;
@@ -455,7 +492,7 @@ struct Cell {
                                           __shfl_sync(full, d.z, src));
             if (lane == src) valid = false;
             if (!check_dup || !has_site(kk)) cut(kk, dd);
-            valid = valid && d2 < 4.f * R2;
+            valid = valid && d2 < 4.f * R2 && may_cut(d, d2);
         }
     }
 };
