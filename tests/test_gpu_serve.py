@@ -115,3 +115,18 @@ def test_open_loop_poisson_stream(foam):
     print("serve", {k: st[k] for k in ("completed", "rejected_open_loop", "p50_ms", "p99_ms",
                                          "mrays_s", "mean_batch", "max_busy_streams")})
     srv.close()
+
+
+def test_fisheye_and_rolling_shutter_requests(foam):
+    # non-pinhole cameras go through the same batches (effects kernels)
+    fish = S.fisheye(48, 40, 190.0, c2w=S.look_at((1.2, 0.9, -0.4)))
+    roll = S.Camera(**{**S.pinhole(40, 30, 60.0, c2w=S.look_at((-1.5, 0.5, 1.0))).__dict__,
+                       "shutter": (0.1, 0.05, 0.0)})
+    srv = Server(foam, mem_budget_bytes=64 << 20, max_inflight=16, n_streams=2, max_batch=4)
+    pins = [S.pinhole(32, 24, 60.0, c2w=S.look_at((2.0, -1.0, 0.3))) for _ in range(3)]
+    ids = [(srv.submit(c), c) for c in pins[:2] + [fish, roll] + pins[2:]]
+    for rid, cam in ids:
+        img = np.zeros((cam.n_rays, 3), np.float32)
+        srv.wait(rid, out=img)
+        np.testing.assert_array_equal(img, _image(foam, cam))
+    srv.close()
