@@ -1007,7 +1007,7 @@ RF_API rf_status rf_adjacency_build(rf_adjacency *a, int64_t n, const float *pos
         P.counters = a->counters;
         P.wide_list = a->wide;
         const int64_t blocks = std::min<int64_t>((n + kWarps - 1) / kWarps, 152 * 256);
-        cell_kernel<kMaxPlanes, kWarps, 6><<<(unsigned)blocks, 32 * kWarps, 0, st>>>(P);
+        cell_kernel<kMaxPlanes, kWarps, 7><<<(unsigned)blocks, 32 * kWarps, 0, st>>>(P);
         RF_CUDA(cudaGetLastError());
         // the cells that overflowed, again with room for more faces
         P.site_list = a->wide;
