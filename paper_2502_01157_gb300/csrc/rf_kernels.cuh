@@ -37,7 +37,7 @@ enum { kPlain = 0, kTrace = 1, kQuant = 2 };
 // the ray and the walk carries on from the same cell (depth then measures the
 // bent path).
 template <typename AT, int DEG, int MODE, bool FX>
-__global__ void __launch_bounds__(kBlock, 8) fwd_kernel(const RenderParams p, const FwdOut out) {
+__global__ void __launch_bounds__(kBlock, FX ? 6 : 8) fwd_kernel(const RenderParams p, const FwdOut out) {
     constexpr bool TRACE = MODE == kTrace;
     constexpr bool QUANT = MODE == kQuant;
     const PixelTask px = pixel_of_thread(p.lc);
