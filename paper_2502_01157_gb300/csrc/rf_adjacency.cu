@@ -906,7 +906,8 @@ RF_API rf_status rf_adjacency_destroy(rf_adjacency *a) {
 RF_API rf_status rf_adjacency_build(rf_adjacency *a, int64_t n, const float *pos, const float *domain6,
                                     int32_t incremental, void *stream) {
     if (!a || !pos) return fail(RF_ERR_INVALID_ARG, "adjacency and pos are required");
-    if (n < 1 || n >= (1ll << 30)) return fail(RF_ERR_INVALID_ARG, "n_sites must be in [1, 2^30)");
+    // the lists are int32 CSR: ~16 edges per site keeps 10^8 sites below 2^31 edges
+    if (n < 1 || n > 100000000) return fail(RF_ERR_INVALID_ARG, "n_sites must be in [1, 10^8]");
     if (incremental && (a->n != n || !a->off))
         return fail(RF_ERR_INVALID_ARG, "an incremental rebuild needs a previous build of as many sites");
     cudaStream_t st = (cudaStream_t)stream;
