@@ -451,9 +451,9 @@ RF_API rf_status rf_sample_multinomial(const float *weights, int64_t n, const fl
  * sorted by neighbour id, without self loops: ready for rf_scene_desc.
  *
  * rf_adjacency_build: pos device float [n_sites][3] (1 <= n_sites <= 10^8);
- *   domain6 HOST float[6]
- *   (min xyz, max xyz) holding every site, or NULL for the sites' bounding
- *   box grown by 5% of its extent (at least 1e-3) on every side.  Faces that
+ *   domain6 HOST float[6] (min xyz, max xyz) holding every site, or NULL for
+ *   the sites' bounding box grown by 5% of its extent (at least 1e-3) on
+ *   every side.  Faces that
  *   lie entirely outside the domain are not produced, so the domain should
  *   hold the cameras as well as the sites.  incremental = 1 seeds each cell
  *   with its previous neighbours (the sites moved a little since the last
