@@ -1,6 +1,6 @@
 """Helpers for the CUDA-vs-oracle parity tests.
 
-Tolerances (the arithmetic behind them is explained in the design doc):
+Tolerances:
 
 * visited cells: bit-exact on every ray the oracle does not flag as
   near-degenerate;
