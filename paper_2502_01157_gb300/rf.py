@@ -262,11 +262,16 @@ class Foam:
     """
 
     def __init__(self, pos, adj_off, adj_idx, density, sh, aabb=None, stream=None):
-        L = lib()
         self.pos = pos.contiguous()
+        self._aabb = aabb
+        self._attrs(density, sh)
+        self._create(adj_off, adj_idx, stream)
+
+    def _create(self, adj_off, adj_idx, stream=None):
+        L = lib()
+        aabb = self._aabb
         self.adj_off = adj_off.to(torch.int32).contiguous()
         self.adj_idx = adj_idx.to(torch.int32).contiguous()
-        self._attrs(density, sh)
         d = rf_scene_desc()
         d.n_sites = int(self.pos.shape[0])
         d.n_edges = int(self.adj_idx.shape[0])
@@ -316,7 +321,26 @@ class Foam:
         off, idx = builder.build(pos, domain=domain, stream=stream)
         foam = cls(pos, off, idx, density, sh, aabb=aabb, stream=stream)
         foam.adjacency_stats = builder.stats
+        foam._builder = builder
         return foam
+
+    def rebuild_adjacency(self, builder=None, domain=None, incremental: bool = False, stream=None):
+        """Rebuild the neighbour lists on the GPU from the current positions
+        (after position steps) and re-pack the foam with them.  ``builder``:
+        an :class:`Adjacency` kept between rebuilds (one is made and kept on
+        the foam otherwise); ``incremental`` seeds each cell with its previous
+        neighbours (the builder's previous result)."""
+        if builder is None:
+            builder = getattr(self, "_builder", None) or Adjacency()
+            self._builder = builder
+        off, idx = builder.build(self.pos, domain=domain, incremental=incremental, stream=stream)
+        old = self._h
+        self._h = None
+        self._create(off, idx, stream)
+        if old is not None:
+            lib().rf_scene_destroy(old)
+        self.adjacency_stats = builder.stats
+        return builder.stats
 
     @property
     def handle(self):
