@@ -330,3 +330,42 @@ def test_backward_with_bounces_matches_finite_differences(ior):
             assert G["sh"][i, k, 1] == pytest.approx(fd(sc.sh, (i, k, 1), 1e-6), rel=1e-5, abs=1e-8)
         for a in range(3):
             assert G["pos"][i, a] == pytest.approx(fd(sc.pos, (i, a), 1e-6), rel=1e-4, abs=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# near-degenerate flags (conditioning of the FP32 comparison)
+# ---------------------------------------------------------------------------
+def _two_cells():
+    pos = np.array([[-1.0, 0, 0], [1.0, 0, 0]], np.float32)
+    return TinyScene(pos, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32),
+                     np.array([0.5, 0.5], np.float32), np.zeros((2, 1, 3), np.float32), 0,
+                     np.full(3, -1.0, np.float32), np.full(3, 1.0, np.float32))
+
+
+@pytest.mark.parametrize("theta,delta,flagged", [(1e-5, 1e-6, True), (1e-3, 1e-4, False), (0.5, 0.05, False)])
+def test_grazing_face_crossing_is_flagged(theta, delta, flagged):
+    # the ray crosses the face x = 0 at t = delta / sin(theta), at an angle
+    # whose cosine to the face normal is sin(theta)
+    sc = _two_cells()
+    cam = _ray_cam((-delta, -0.9, 0.0), (math.sin(theta), math.cos(theta), 0.0))
+    out = oracle.render(sc, cam, trace=8)
+    assert list(out["trace_cells"][0][:2]) == [0, 1]      # it does cross
+    assert bool(out["degen"][0]) == flagged
+
+
+@pytest.mark.parametrize("h,flagged", [(0.5 * math.sqrt(1 - 1e-3), True), (0.3, False)])
+def test_near_grazing_sphere_hit_is_flagged(h, flagged):
+    sc = _one_cell(0.3, (0.5, 0.5, 0.5), 3.0)
+    cam = _ray_cam((-2.0, h, 0.0), (1.0, 0.0, 0.0))
+    out = oracle.render(sc, cam, effects=S.Sphere((0, 0, 0), 0.5, ior=0.0))
+    assert bool(out["degen"][0]) == flagged
+
+
+@pytest.mark.parametrize("b,flagged", [(1 / 1.5 * 1.0001, True), (0.3, False)])
+def test_critical_angle_is_flagged(b, flagged):
+    # from inside a glass sphere (n = 1.5) the ray meets the surface at
+    # sin(theta_i) = b / r: total internal reflection starts at b = r / n
+    sc = _one_cell(0.3, (0.5, 0.5, 0.5), 3.0)
+    cam = _ray_cam((0.0, b, 0.0), (1.0, 0.0, 0.0))
+    out = oracle.render(sc, cam, effects=S.Sphere((0, 0, 0), 1.0, ior=1.5, max_bounces=1))
+    assert bool(out["degen"][0]) == flagged
