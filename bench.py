@@ -287,14 +287,18 @@ def effects_extras(S, rf, foam, cam, target, scale, loss, grads, args, dev):
                depth=torch.empty(R, device=dev))
     ev = lambda: torch.cuda.Event(enable_timing=True)
     res = {"recipe": "c3 scene, 1920x1080: fisheye 200 deg; rolling shutter (0.02, 0, 0.01) over the "
-                     "frame; glass (n = 1.5) / mirror sphere r = 0.25 at 0.5 along the view axis"}
+                     "frame; glass (n = 1.5) / mirror sphere r = 0.25 at 0.5 along the view axis; the "
+                     f"training step replays a {RECORD_STEPS}-step walk record"}
+    # the training step keeps the forward's walk record, as the headline step does
+    tout = dict(out, walk_record=(torch.empty(rf.walk_record_bytes([cam], RECORD_STEPS), dtype=torch.uint8,
+                                              device=dev), RECORD_STEPS))
     for name, c, sph in (("fisheye", fish, None), ("rolling_shutter", roll, None),
                          ("glass_sphere", cam, glass), ("mirror_sphere", cam, mirror),
                          ("fisheye_glass", fish, glass)):
         def fstep():
-            foam.render([c], out=out, effects=sph)
-            d_rgb, _ = rf.mse_grad(out["rgb"], target, scale, loss)
-            foam.backward([c], out, d_rgb, grads=grads, effects=sph)
+            foam.render([c], out=tout, effects=sph)
+            d_rgb, _ = rf.mse_grad(tout["rgb"], target, scale, loss)
+            foam.backward([c], tout, d_rgb, grads=grads, effects=sph)
 
         chk = foam.render([c], steps=True, effects=sph)
         k = float(chk["steps"].float().mean().item())
@@ -698,7 +702,7 @@ def main():
             "cell_steps_per_s": steps_total / (ms * 1e-3),
             **res,
             "mixture_3m": mixture,
-            "gpu_launches": args.steps * 5,
+            "gpu_launches": args.steps * 6,
             "roofline": roof,
             "clocks": clk,
             "e2e": {"value": R / e2e_s / 1e6, "unit": UNIT,

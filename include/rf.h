@@ -248,7 +248,8 @@ RF_API rf_status rf_render_bwd(rf_scene *scene, const rf_camera *cams, int32_t n
  *                        rf_render_bwd_ex with the same cameras, options and
  *                        scene, it lets the backward replay those steps
  *                        instead of searching the faces again; the gradients
- *                        are the same bits either way.
+ *                        are the same up to the order of the floating-point
+ *                        atomics.
  */
 typedef struct rf_fwd_outputs {
     float *rgb;
@@ -270,7 +271,12 @@ typedef struct rf_fwd_outputs {
  *     walk_record            optional: the forward's walk record (same
  *                            walk_record_bytes and walk_record_steps)
  *   gradients (device, FP32, accumulated +=, each may be NULL):
- *     density [N], sh [N][(deg+1)^2][3], pos [N][3] */
+ *     density [N], sh [N][(deg+1)^2][3], pos [N][3]
+ *   With density or pos requested, the first backward on a scene allocates a
+ *   16-byte-per-site workspace owned by the scene (counted in rf_scene_info's
+ *   device_bytes; RF_ERR_OOM if it cannot), and every backward zeroes it on
+ *   the stream, sums the site terms into it and adds it to pos and density
+ *   after the walk. */
 typedef struct rf_bwd_inputs {
     const float *rgb;
     const float *trans;

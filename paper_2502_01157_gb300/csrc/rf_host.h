@@ -27,6 +27,7 @@ struct rf_scene {
     unsigned long long *start_keys = nullptr;  // workspace [kMaxCamsPerLaunch]
     int32_t *flags = nullptr;                  // workspace [8] (validation counters)
     int32_t sh_v8 = 0;                         // SH rows 32-byte aligned
+    float4 *g_acc = nullptr;                   // workspace [N] of the backward (first use)
     size_t bytes = 0;
     int device = 0;
 };

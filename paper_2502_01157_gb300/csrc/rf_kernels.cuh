@@ -134,6 +134,8 @@ struct BwdIO {
     const float *d_rgb, *d_trans, *d_depth;
     float *g_density, *g_sh, *g_pos;
     int32_t sh_vec;  // g_sh rows may use 16-byte atomics
+    float4 *g_acc;   // [n_sites] {position x, y, z, density} gradient sums, added
+                     // to g_pos / g_density after the launch (null: neither is wanted)
     const float *qaux, *d_quantile;
 };
 
@@ -172,16 +174,18 @@ __device__ __forceinline__ void scatter_sh(float *__restrict__ g_sh, int i, cons
 // addresses many times.  Each iteration the lanes stage their contributions
 // (SH row, density, the two site positions of the crossing that entered the
 // cell) in shared memory; lanes with the same (previous cell, cell) pair are
-// summed column-wise and the sum is added with one coalesced atomic per
-// value.  A warp whose lanes are spread over many cells scatters per lane.
+// summed column-wise and the sums are added with 16-byte vector atomics: the
+// SH row into g_sh, the site terms into the {x, y, z, density} accumulator
+// g_acc that a final pass adds to g_pos and g_density.  A warp whose lanes
+// are spread over many cells scatters per lane.
 constexpr int kMaxGroups = 12;
 
 template <typename AT, int DEG, bool QUANT, bool FX>
 __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, const BwdIO io) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int NV = 3 * K;       // SH gradient row
-    constexpr int V = NV + 7;       // + density, position of the cell, position of the previous cell
-    constexpr int VP = (V + 3) / 4 * 4;
+    constexpr int NV = 3 * K;              // SH gradient row
+    constexpr int NVP = (NV + 3) / 4 * 4;  // padded to whole 16-byte columns
+    constexpr int VP = NVP + 8;            // + {position of the cell, density}, {position of the previous cell, 0}
     // row stride: a multiple of 4 floats (16-byte row stores) whose quarter is
     // odd, so the 8 lanes of a 128-bit store phase hit 8 different bank quads;
     // a column read (one row, consecutive columns) is conflict-free for any stride
@@ -402,14 +406,10 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
         const bool grouped = __popc(leaders) <= kMaxGroups;
         if (live && (!shared_row || !grouped)) {
             if (io.g_sh && (cb[0] != 0.f || cb[1] != 0.f || cb[2] != 0.f)) scatter_sh<DEG>(io.g_sh, i, cb, Y, io.sh_vec);
-            if (sig_bar != 0.f) atomicAdd(io.g_density + i, sig_bar);
-            if (key_prev >= 0 && io.g_pos) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (gpos_i[a] != 0.f) atomicAdd(io.g_pos + 3 * (int64_t)i + a, gpos_i[a]);
-                    if (gpos_a[a] != 0.f) atomicAdd(io.g_pos + 3 * (int64_t)key_prev + a, gpos_a[a]);
-                }
-            }
+            if (sig_bar != 0.f || gpos_i[0] != 0.f || gpos_i[1] != 0.f || gpos_i[2] != 0.f)
+                atomicAdd(io.g_acc + i, make_float4(gpos_i[0], gpos_i[1], gpos_i[2], sig_bar));
+            if (key_prev >= 0 && (gpos_a[0] != 0.f || gpos_a[1] != 0.f || gpos_a[2] != 0.f))
+                atomicAdd(io.g_acc + key_prev, make_float4(gpos_a[0], gpos_a[1], gpos_a[2], 0.f));
         }
         if (grouped && leaders) {
             if (shared_row) {
@@ -423,9 +423,10 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                     for (int e = 0; e < 4; ++e) {
                         const int c = 4 * q4 + e;
                         v[e] = c < NV ? cb[c % 3] * Y[c / 3]
-                             : c == NV ? sig_bar
-                             : c < NV + 4 ? gpos_i[(c - NV - 1) % 3]
-                             : c < NV + 7 ? gpos_a[(c - NV - 4) % 3] : 0.f;
+                             : c < NVP ? 0.f
+                             : c < NVP + 3 ? gpos_i[c - NVP]
+                             : c == NVP + 3 ? sig_bar
+                             : c < NVP + 7 ? gpos_a[c - NVP - 4] : 0.f;
                     }
                     row[q4] = make_float4(v[0], v[1], v[2], v[3]);
                 }
@@ -470,21 +471,18 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                     }
                     const int c = 4 * hl;
                     const bool nz = sm.x != 0.f || sm.y != 0.f || sm.z != 0.f || sm.w != 0.f;
-                    if (NV % 4 == 0 && c + 3 < NV && io.sh_vec) {
-                        if (nz) atomicAdd(reinterpret_cast<float4 *>(io.g_sh + (size_t)cell_i * NV + c), sm);
-                    } else if (nz) {
+                    if (!nz) {
+                    } else if (c >= NVP) {
+                        // {position, density} of the cell, {position, 0} of the previous cell
+                        if (c == NVP) atomicAdd(io.g_acc + cell_i, sm);
+                        else if (cell_a >= 0) atomicAdd(io.g_acc + cell_a, sm);
+                    } else if (NV % 4 == 0 && io.sh_vec) {
+                        atomicAdd(reinterpret_cast<float4 *>(io.g_sh + (size_t)cell_i * NV + c), sm);
+                    } else {
                         const float v4[4] = {sm.x, sm.y, sm.z, sm.w};
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int col = c + j;
-                            const float sum = v4[j];
-                            if (col < V && sum != 0.f) {
-                                if (col < NV) atomicAdd(io.g_sh + (size_t)cell_i * NV + col, sum);
-                                else if (col == NV) atomicAdd(io.g_density + cell_i, sum);
-                                else if (col < NV + 4) atomicAdd(io.g_pos + 3 * (int64_t)cell_i + (col - NV - 1), sum);
-                                else if (cell_a >= 0) atomicAdd(io.g_pos + 3 * (int64_t)cell_a + (col - NV - 4), sum);
-                            }
-                        }
+                        for (int j = 0; j < 4; ++j)
+                            if (c + j < NV && v4[j] != 0.f) atomicAdd(io.g_sh + (size_t)cell_i * NV + c + j, v4[j]);
                     }
                 }
             }

@@ -48,6 +48,20 @@ __global__ void mse_grad_kernel(const float *__restrict__ rgb, const float *__re
     if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, scale * acc);
 }
 
+// g_pos[i] += acc[i].xyz, g_density[i] += acc[i].w: the per-site sums the
+// backward's vector atomics collected.
+__global__ void add_site_grads_kernel(const float4 *__restrict__ acc, int64_t n, float *g_pos, float *g_density) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = acc[i];
+        if (g_pos) {
+            g_pos[3 * i + 0] += a.x;
+            g_pos[3 * i + 1] += a.y;
+            g_pos[3 * i + 2] += a.z;
+        }
+        if (g_density) g_density[i] += a.w;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -188,8 +202,22 @@ RF_API rf_status rf_render_bwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_
         return fail(RF_ERR_INVALID_ARG, "quantile_aux is required with d_quantile");
     if (!gr->density && !gr->sh && !gr->pos) return RF_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    // the per-site {position, density} sums: a scene-owned workspace of 16
+    // bytes per site, allocated by the first backward and zeroed by each
+    if ((gr->pos || gr->density) && !s->g_acc) {
+        cudaError_t e = cudaMalloc((void **)&s->g_acc, sizeof(float4) * (size_t)s->n_sites);
+        if (e != cudaSuccess) {
+            s->g_acc = nullptr;
+            return e == cudaErrorMemoryAllocation ? fail(RF_ERR_OOM, "backward workspace (%lld bytes)",
+                                                         (long long)(sizeof(float4) * s->n_sites))
+                                                  : cuda_fail(e, "cudaMalloc(g_acc)");
+        }
+        s->bytes += sizeof(float4) * (size_t)s->n_sites;
+    }
+    float4 *acc = (gr->pos || gr->density) ? s->g_acc : nullptr;
+    if (acc) RF_CUDA(cudaMemsetAsync(acc, 0, sizeof(float4) * (size_t)s->n_sites, st));
     BwdIO io = {in->rgb, in->trans, in->depth, in->d_rgb, in->d_trans, in->d_depth, gr->density,
-                gr->sh, gr->pos, (int32_t)(((uintptr_t)gr->sh & 15) == 0), in->quantile_aux,
+                gr->sh, gr->pos, (int32_t)(((uintptr_t)gr->sh & 15) == 0), acc, in->quantile_aux,
                 in->d_quantile};
     const bool quant = in->d_quantile != nullptr;
     RenderParams p;
@@ -214,6 +242,11 @@ RF_API rf_status rf_render_bwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_
         p.rec = in->walk_record ? const_cast<uint8_t *>(in->walk_record) + rec_off : nullptr;
         if (in->walk_record) rec_off += record_bytes_of(cams, first, count, in->walk_record_steps);
         launch_bwd_fx(p, s->attr_dtype, s->sh_degree, quant, tiles, io, st);
+        RF_CUDA(cudaGetLastError());
+    }
+    if (acc) {
+        const int64_t blocks = std::min<int64_t>((s->n_sites + 255) / 256, 152 * 8);
+        add_site_grads_kernel<<<(unsigned)blocks, 256, 0, st>>>(acc, s->n_sites, gr->pos, gr->density);
         RF_CUDA(cudaGetLastError());
     }
     return RF_OK;

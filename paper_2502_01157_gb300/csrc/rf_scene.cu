@@ -306,6 +306,7 @@ static void free_scene(rf_scene *s) {
     cudaFree(s->nbr);
     cudaFree(s->start_keys);
     cudaFree(s->flags);
+    cudaFree(s->g_acc);
     delete s;
 }
 
