@@ -100,7 +100,7 @@ def kernel_source_hash():
 
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2502_01157_gb300", "csrc")
-    for name in ("rf_internal.cuh", "rf_kernels.cuh", "rf_render.cu", "rf_scene.cu"):
+    for name in ("rf_host.h", "rf_internal.cuh", "rf_kernels.cuh", "rf_render.cu", "rf_scene.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
