@@ -245,6 +245,12 @@ def test_invalid_inputs_are_rejected():
     with pytest.raises(rf.RFError) as e:
         foam.render([bad])
     assert e.value.code == 1
+    # no camera, or a camera without pixels: rejected before anything runs
+    for cams in ([], [camera_at((0.0, 0.0, 0.0), (1.0, 0.0, 0.0), w=0, h=4)],
+                 [camera_at((0.0, 0.0, 0.0), (1.0, 0.0, 0.0), w=4, h=0)]):
+        with pytest.raises(rf.RFError) as e:
+            foam.render(cams)
+        assert e.value.code == 1
     # asymmetric adjacency
     off, idx = csr_from_lists([[1], [], [0]])
     with pytest.raises(rf.RFError) as e:
