@@ -190,13 +190,11 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
     // odd, so the 8 lanes of a 128-bit store phase hit 8 different bank quads;
     // a column read (one row, consecutive columns) is conflict-free for any stride
     constexpr int SP = ((VP / 4) % 2 == 1) ? VP : VP + 4;
-    // 32 lane rows + one zero row that pads the 4-member unrolled sums
-    __shared__ __align__(16) float stage_all[kBlock / 32][33 * SP];
+    // one row per lane
+    __shared__ __align__(16) float stage_all[kBlock / 32][32 * SP];
     const int lane = threadIdx.x & 31;
     float *stage = stage_all[threadIdx.x >> 5];
     const unsigned full = 0xffffffffu;
-    for (int c = lane; c < SP; c += 32) stage[32 * SP + c] = 0.f;
-    __syncwarp();
 
     // per-lane set-up; no early return: every lane takes part in the
     // warp-wide scatter until the whole warp is done
@@ -451,19 +449,22 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                 const int cell_a = __shfl_sync(full, key_prev, L);
                 if ((lane < 16 || two) && hl < NQ) {
                     // four members per pass with independent loads; an absent
-                    // member reads the zero row 32
-                    float4 sm = make_float4(0.f, 0.f, 0.f, 0.f);
+                    // member (-1) loads nothing
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 sm = z4;
                     for (unsigned mm = m; mm;) {
                         const int k0 = __ffs(mm) - 1;
                         mm &= mm - 1;
-                        const int k1 = mm ? __ffs(mm) - 1 : 32;
+                        const int k1 = __ffs(mm) - 1;
                         mm &= mm - 1;
-                        const int k2 = mm ? __ffs(mm) - 1 : 32;
+                        const int k2 = __ffs(mm) - 1;
                         mm &= mm - 1;
-                        const int k3 = mm ? __ffs(mm) - 1 : 32;
+                        const int k3 = __ffs(mm) - 1;
                         mm &= mm - 1;
-                        const float4 a0 = stage4[k0 * SQ + hl], a1 = stage4[k1 * SQ + hl];
-                        const float4 a2 = stage4[k2 * SQ + hl], a3 = stage4[k3 * SQ + hl];
+                        const float4 a0 = stage4[k0 * SQ + hl];
+                        const float4 a1 = k1 >= 0 ? stage4[k1 * SQ + hl] : z4;
+                        const float4 a2 = k2 >= 0 ? stage4[k2 * SQ + hl] : z4;
+                        const float4 a3 = k3 >= 0 ? stage4[k3 * SQ + hl] : z4;
                         sm.x += (a0.x + a1.x) + (a2.x + a3.x);
                         sm.y += (a0.y + a1.y) + (a2.y + a3.y);
                         sm.z += (a0.z + a1.z) + (a2.z + a3.z);
