@@ -190,11 +190,16 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
     // odd, so the 8 lanes of a 128-bit store phase hit 8 different bank quads;
     // a column read (one row, consecutive columns) is conflict-free for any stride
     constexpr int SP = ((VP / 4) % 2 == 1) ? VP : VP + 4;
-    // one row per lane
-    __shared__ __align__(16) float stage_all[kBlock / 32][32 * SP];
+    // one row per lane (+ a zero row that absent members read in the FX kernels)
+    constexpr int ROWS = FX ? 33 : 32;
+    __shared__ __align__(16) float stage_all[kBlock / 32][ROWS * SP];
     const int lane = threadIdx.x & 31;
     float *stage = stage_all[threadIdx.x >> 5];
     const unsigned full = 0xffffffffu;
+    if constexpr (FX) {
+        for (int c = lane; c < SP; c += 32) stage[32 * SP + c] = 0.f;
+        __syncwarp();
+    }
 
     // per-lane set-up; no early return: every lane takes part in the
     // warp-wide scatter until the whole warp is done
@@ -462,9 +467,16 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                         const int k3 = __ffs(mm) - 1;
                         mm &= mm - 1;
                         const float4 a0 = stage4[k0 * SQ + hl];
-                        const float4 a1 = k1 >= 0 ? stage4[k1 * SQ + hl] : z4;
-                        const float4 a2 = k2 >= 0 ? stage4[k2 * SQ + hl] : z4;
-                        const float4 a3 = k3 >= 0 ? stage4[k3 * SQ + hl] : z4;
+                        float4 a1, a2, a3;
+                        if constexpr (FX) {
+                            a1 = stage4[(k1 >= 0 ? k1 : 32) * SQ + hl];
+                            a2 = stage4[(k2 >= 0 ? k2 : 32) * SQ + hl];
+                            a3 = stage4[(k3 >= 0 ? k3 : 32) * SQ + hl];
+                        } else {
+                            a1 = k1 >= 0 ? stage4[k1 * SQ + hl] : z4;
+                            a2 = k2 >= 0 ? stage4[k2 * SQ + hl] : z4;
+                            a3 = k3 >= 0 ? stage4[k3 * SQ + hl] : z4;
+                        }
                         sm.x += (a0.x + a1.x) + (a2.x + a3.x);
                         sm.y += (a0.y + a1.y) + (a2.y + a3.y);
                         sm.z += (a0.z + a1.z) + (a2.z + a3.z);
