@@ -417,7 +417,10 @@ class Foam:
                  effects=None) -> dict:
         """Accumulate gradients (density, sh, pos; float32) of the forward
         outputs (and of the quantile loss, with ``d_quantile``) into ``grads``
-        (zero-initialised if None)."""
+        (zero-initialised if None).  A ``fwd`` that holds a ``walk_record``
+        is replayed instead of searched again.  The first backward that asks
+        for density or position gradients allocates a 16-byte-per-site
+        workspace owned by the scene."""
         if grads is None:
             dev = self.pos.device
             grads = dict(density=torch.zeros(self.n_sites, device=dev),
