@@ -90,3 +90,48 @@ def test_walk_record_bytes_without_gpu(L):
     ca = rf.camera_array(cams)
     assert L.rf_walk_record_bytes(ca, len(ca), 0) == 0
     assert L.rf_walk_record_bytes(None, 3, 8) == 0
+
+
+def test_null_handles_and_pointers_are_rejected_on_the_host(L):
+    """Every entry point that takes a handle or a required pointer returns
+    RF_ERR_INVALID_ARG for NULL before it touches the device, and the
+    destroy calls accept NULL."""
+    from paper_2502_01157_gb300 import scenes as S
+    INVALID = 1
+    cam = rf.camera_array([S.pinhole(8, 8, 60.0)])
+    opts = rf.opts_struct()
+    n64, e64 = ctypes.c_int64(), ctypes.c_int64()
+    calls = {
+        "rf_scene_set_attributes": lambda: L.rf_scene_set_attributes(None, None, None, 0),
+        "rf_scene_update_positions": lambda: L.rf_scene_update_positions(None, None, None),
+        "rf_scene_info": lambda: L.rf_scene_info(None, ctypes.byref(n64), ctypes.byref(e64), None, None),
+        "rf_render_bwd": lambda: L.rf_render_bwd(None, cam, 1, ctypes.byref(opts), None, None, None, None,
+                                                 None, None, None, None, None, None),
+        "rf_render_bwd_ex": lambda: L.rf_render_bwd_ex(None, cam, 1, ctypes.byref(opts), None, None, None),
+        "rf_trace_cells": lambda: L.rf_trace_cells(None, cam, ctypes.byref(opts), 4, None, None, None),
+        "rf_mse_grad": lambda: L.rf_mse_grad(None, None, 3, 1.0, None, None, None),
+        "rf_adjacency_create": lambda: L.rf_adjacency_create(None),
+        "rf_adjacency_build": lambda: L.rf_adjacency_build(None, 10, None, None, 0, None),
+        "rf_adjacency_result": lambda: L.rf_adjacency_result(None, None, None, None),
+        "rf_adjacency_copy": lambda: L.rf_adjacency_copy(None, None, None, None),
+        "rf_serve_create": lambda: L.rf_serve_create(None, None, None),
+        "rf_serve_submit": lambda: L.rf_serve_submit(None, cam, None),
+        "rf_serve_poll": lambda: L.rf_serve_poll(None, 0, None, None, None),
+        "rf_serve_wait": lambda: L.rf_serve_wait(None, 0, 0, None, None),
+        "rf_serve_stats": lambda: L.rf_serve_stats(None, None),
+        "rf_serve_reset_stats": lambda: L.rf_serve_reset_stats(None),
+        "rf_densify_scores": lambda: L.rf_densify_scores(None, None, None, None),
+        "rf_prune_mask": lambda: L.rf_prune_mask(None, 0.1, None, None),
+        "rf_sample_multinomial": lambda: L.rf_sample_multinomial(None, 4, None, 2, None, 0, None, None),
+        "rf_render_fwd_noalloc": lambda: L.rf_render_fwd_noalloc(0, 0, None, None, None, None, None, 0, 0, None,
+                                                                 cam, 1, ctypes.byref(opts), None, None, None,
+                                                                 None),
+    }
+    for name, call in calls.items():
+        assert call() == INVALID, name
+        assert L.rf_last_error(), name
+    # nothing to do: a zero-length loss and zero-size workspaces
+    assert L.rf_mse_grad(None, None, 0, 1.0, None, None, None) == INVALID   # pointers still required
+    assert L.rf_multinomial_workspace_bytes(0) == 0
+    for destroy in ("rf_scene_destroy", "rf_adjacency_destroy", "rf_serve_destroy"):
+        assert getattr(L, destroy)(None) == 0, destroy
