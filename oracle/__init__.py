@@ -37,6 +37,25 @@ _lib = None
 RAY_OK = 0
 RAY_MAX_STEPS = 1
 
+# Near-degenerate ray classes (bit flags of ``render(...)["flags"]``): why a
+# correct FP32 renderer may differ from this FP64 walk on a ray.
+FLAG_EDGE = 1     # passes within tau of a Voronoi edge or vertex: the next cell is a tie
+FLAG_CAMERA = 2   # the start point is within tau of the bisector of its two nearest sites
+FLAG_STOP = 4     # T within a relative 1e-3 of eps at a stop test: may stop one step apart
+FLAG_GRAZE = 8    # a face crossed at grazing incidence: ill-conditioned position gradient
+FLAG_BEND = 16    # sphere hit near tangency / refraction near the critical angle
+FLAG_NAMES = {FLAG_EDGE: "edge", FLAG_CAMERA: "camera", FLAG_STOP: "stop", FLAG_GRAZE: "graze",
+              FLAG_BEND: "bend"}
+
+
+def flag_counts(flags) -> dict:
+    """Number of rays in each near-degenerate class (a ray may be in several)."""
+    f = np.asarray(flags)
+    out = {name: int(np.count_nonzero(f & bit)) for bit, name in FLAG_NAMES.items()}
+    out["any"] = int(np.count_nonzero(f))
+    out["rays"] = int(f.size)
+    return out
+
 _d = ctypes.POINTER(ctypes.c_double)
 _i64 = ctypes.POINTER(ctypes.c_int64)
 _i32 = ctypes.POINTER(ctypes.c_int32)
@@ -173,9 +192,14 @@ def nearest_site(pos, q):
 def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
            tau=None, trace: int = 0, threads: int = 0, effects=None) -> dict:
     """Forward render (Alg. 1, Eq. 3-4).  Returns rgb [R,3], trans [R], depth [R],
-    steps [R], status [R], degen [R] and, if ``trace > 0``, trace_cells
-    [R,trace] (-1 padded) and trace_t [R,trace].  ``effects``: an analytic
-    sphere the rays reflect off or refract through (``scenes.Sphere``)."""
+    steps [R], status [R] and, if ``trace > 0``, trace_cells [R,trace] (-1
+    padded) and trace_t [R,trace].  ``effects``: an analytic sphere the rays
+    reflect off or refract through (``scenes.Sphere``).
+
+    Near-degenerate rays: ``flags`` [R] (FLAG_* bits) and three views of it:
+    ``tie`` (EDGE or CAMERA: the visited cells may differ at FP32), ``stop_tie``
+    (STOP: the walk may end one step earlier or later) and ``degen`` (any
+    flag: the gradient may carry the conditioning error)."""
     fx = _fx(effects)
     S = _SceneF64(scene)
     c = _cam(cam)
@@ -188,17 +212,19 @@ def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
     dp = np.zeros(R)
     st = np.zeros(R, np.int32)
     ss = np.zeros(R, np.uint8)
-    dg = np.zeros(R, np.uint8)
+    fl = np.zeros(R, np.uint8)
     tc = np.full((R, max(trace, 1)), -1, np.int32)
     tt = np.full((R, max(trace, 1)), np.nan)
     rc = lib().orc_render(S.n, _p(S.pos, _d), _p(S.off, _i64), _p(S.adj, _i32), _p(S.sigma, _d),
                           _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d), R, _p(px, _i64),
                           float(eps), int(max_steps), tau, _p(rgb, _d), _p(tr, _d), _p(dp, _d),
-                          _p(st, _i32), _p(ss, _u8), _p(dg, _u8), int(trace), _p(tc, _i32),
+                          _p(st, _i32), _p(ss, _u8), _p(fl, _u8), int(trace), _p(tc, _i32),
                           _p(tt, _d), _p(fx, _d), int(threads))
     if rc:
         raise ValueError("oracle render: bad arguments")
-    out = dict(rgb=rgb, trans=tr, depth=dp, steps=st, status=ss, degen=dg.astype(bool), tau=tau)
+    out = dict(rgb=rgb, trans=tr, depth=dp, steps=st, status=ss, flags=fl, tau=tau,
+               tie=(fl & (FLAG_EDGE | FLAG_CAMERA)) != 0, stop_tie=(fl & FLAG_STOP) != 0,
+               degen=fl != 0)
     if trace > 0:
         out["trace_cells"] = tc
         out["trace_t"] = tt

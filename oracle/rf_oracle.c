@@ -50,11 +50,27 @@
  *   - depth = sum_n T_n alpha_n (a_n + b_n) / 2, the weighted midpoint of the
  *     composited part [a_n, b_n] of each segment.
  *
- * Near-degenerate rays: a ray is flagged when (a) some step's end point lies
- * within tau of the plane of another face of the same cell, (b) the camera
- * lies within tau of the bisector of its two nearest sites, or (c) the
- * transmittance is within a relative 1e-3 of eps at a stop test.  On such rays
- * a correct FP32 renderer may visit a different cell sequence.
+ * Near-degenerate rays.  The per-ray flags say why a correct FP32 renderer
+ * may differ from this FP64 walk on a ray (tau = the degeneracy distance):
+ *   ORC_FLAG_EDGE    the ray passes within tau of a Voronoi edge or vertex
+ *                    of a cell it walks: the distance from the ray to the
+ *                    line where the exit plane meets another face plane of
+ *                    the cell (or the scene box), or from a step's end point
+ *                    to another face plane, is below tau (on a leg after a
+ *                    sphere bounce, tau plus the FP32 error bound of the bent
+ *                    ray).  Which cell comes next is then a tie at FP32.
+ *   ORC_FLAG_CAMERA  the start point lies within tau of the bisector of its
+ *                    two nearest sites (nn(o) is a tie).
+ *   ORC_FLAG_STOP    the transmittance is within a relative 1e-3 of eps at a
+ *                    stop test (the walk may end one step earlier or later).
+ *   ORC_FLAG_GRAZE   a face is crossed at grazing incidence: the cells are
+ *                    not in doubt, but the crossing's position gradient
+ *                    (1 / cos) is ill-conditioned at FP32.
+ *   ORC_FLAG_BEND    a sphere hit near tangency or a refraction near the
+ *                    critical angle: the bent direction is ill-conditioned.
+ * EDGE and CAMERA rays may visit other cells; STOP rays may stop one step
+ * apart; GRAZE and BEND rays visit the same cells but their gradients carry
+ * the conditioning error.
  */
 #include <math.h>
 #include <stdint.h>
@@ -66,6 +82,12 @@
 
 #define ORC_RAY_OK 0
 #define ORC_RAY_MAX_STEPS 1
+
+#define ORC_FLAG_EDGE 1
+#define ORC_FLAG_CAMERA 2
+#define ORC_FLAG_STOP 4
+#define ORC_FLAG_GRAZE 8
+#define ORC_FLAG_BEND 16
 
 /* ------------------------------------------------------------------------ */
 /* Real spherical harmonics (orthonormal on the unit sphere, no Condon-      */
@@ -319,24 +341,91 @@ static void cell_colour(const scene_t *S, int64_t i, const double *Y, double *pr
     }
 }
 
+/* Unit normal n and offset h of the bisector plane of sites i and k
+ * ({x : n.x = h}, n pointing from x_i to x_k); returns |x_k - x_i|. */
+static double bisector_plane(const scene_t *S, int64_t i, int64_t k, double *n, double *h)
+{
+    double len2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        n[a] = S->pos[3 * k + a] - S->pos[3 * i + a];
+        len2 += n[a] * n[a];
+    }
+    const double len = sqrt(len2);
+    *h = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        n[a] /= len;
+        *h += n[a] * 0.5 * (S->pos[3 * k + a] + S->pos[3 * i + a]);
+    }
+    return len;
+}
+
 /* Distance from p to the bisector plane of sites i and k. */
 static double plane_dist(const scene_t *S, int64_t i, int64_t k, const double *p)
 {
-    double num = 0.0, nn = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        const double n = S->pos[3 * k + a] - S->pos[3 * i + a];
-        const double m = 0.5 * (S->pos[3 * k + a] + S->pos[3 * i + a]);
-        num += n * (p[a] - m);
-        nn += n * n;
+    double n[3], h;
+    bisector_plane(S, i, k, n, &h);
+    return fabs(n[0] * p[0] + n[1] * p[1] + n[2] * p[2] - h);
+}
+
+/* Distance from the ray piece x(t) = o + t d, t in [w0, w1], to the line
+ * where the planes {na.x = ha} and {nb.x = hb} (unit normals) meet: the
+ * Voronoi edge of the three sites whose bisectors they are.  With the signed
+ * distances s_a(t) = na.x(t) - ha and s_b(t) likewise, and g = na.nb, a
+ * point's squared distance to that line is (s_a^2 + s_b^2 - 2 g s_a s_b) /
+ * (1 - g^2), a convex quadratic in t; its minimum over [w0, w1] is taken at
+ * the clamped stationary point.  Parallel planes have no line: HUGE_VAL. */
+static double ray_line_dist(const double *na, double ha, const double *nb, double hb,
+                            const double *o, const double *d, double w0, double w1)
+{
+    const double g = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
+    const double s2 = 1.0 - g * g;
+    if (!(s2 > 1e-24)) return HUGE_VAL;
+    double aa = -ha, ab = -hb, ca = 0.0, cb = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        aa += na[k] * o[k];
+        ab += nb[k] * o[k];
+        ca += na[k] * d[k];
+        cb += nb[k] * d[k];
     }
-    return fabs(num) / sqrt(nn);
+    const double A = ca * ca + cb * cb - 2.0 * g * ca * cb;
+    const double B = aa * ca + ab * cb - g * (aa * cb + ab * ca);
+    double t = A > 0.0 ? -B / A : w0;
+    if (t < w0) t = w0;
+    if (t > w1) t = w1;
+    const double sa = aa + ca * t, sb = ab + cb * t;
+    const double q = (sa * sa + sb * sb - 2.0 * g * sa * sb) / s2;
+    return q > 0.0 ? sqrt(q) : 0.0;
+}
+
+/* Is a Voronoi edge of cell i within tol of the ray piece [w0, w1]?  The
+ * step ends on the plane {ne.x = he} (the exit face `skip`, or a face of the
+ * scene box); every other face plane k of the cell meets it in a line. */
+static int near_edge(const scene_t *S, int64_t i, int64_t skip, const double *ne, double he,
+                     const double *o, const double *d, double w0, double w1, double tol)
+{
+    for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
+        const int64_t k = S->adj[f];
+        if (k == skip) continue;
+        double nk[3], hk;
+        bisector_plane(S, i, k, nk, &hk);
+        if (ray_line_dist(ne, he, nk, hk, o, d, w0, w1) < tol) return 1;
+    }
+    return 0;
 }
 
 typedef struct {
     double rgb[3], T, depth;
     int32_t steps;
-    uint8_t status, degen;
+    uint8_t status, flags;
 } ray_out_t;
+
+/* FP32 error bound of the current leg's ray: its origin is off by up to e_pos
+ * and its direction by up to e_dir (relative), so a point at parameter t is
+ * off by e_pos + e_dir t.  Both are 0 for the camera's own ray, whose FP32
+ * rounding the degeneracy distance tau already covers. */
+typedef struct {
+    double e_pos, e_dir;
+} leg_err_t;
 
 /*
  * Alg. 1 for one ray.  Segments are appended to L (if non-NULL); the visited
@@ -351,6 +440,7 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
     double o[3] = {o_in[0], o_in[1], o_in[2]}, d[3] = {d_in[0], d_in[1], d_in[2]};
     int64_t i = start;
     int steps = 0, bounces = 0, inside = 0;
+    leg_err_t err = {0.0, 0.0};
     if (E) {
         double r2 = 0.0;
         for (int a = 0; a < 3; ++a) r2 += (o[a] - E->c[a]) * (o[a] - E->c[a]);
@@ -358,11 +448,11 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
     }
     R->status = ORC_RAY_OK;
     while (T > eps) {
-        if (fabs(T - eps) <= 1e-3 * eps) R->degen = 1;
+        if (fabs(T - eps) <= 1e-3 * eps) R->flags |= ORC_FLAG_STOP;
         if (steps >= max_steps) { R->status = ORC_RAY_MAX_STEPS; break; }
         const double *x = S->pos + 3 * i;
         /* nearest front-facing bisector plane (Fig. 3) */
-        double t1 = HUGE_VAL, cos_exit = 1.0, len_exit = 1.0;
+        double t1 = HUGE_VAL, cos_exit = 1.0, len_exit = HUGE_VAL, len_min = 1.0;
         int64_t nxt = -1;
         for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
             const int64_t j = S->adj[f];
@@ -375,26 +465,34 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
                 num += n * (m - o[a]);
                 nn += n * n;
             }
+            if (f == S->off[i] || sqrt(nn) < len_min) len_min = sqrt(nn);
             if (den > 0.0) {
                 const double t = num / den;
                 if (t < t1) { t1 = t; nxt = j; cos_exit = den / sqrt(nn); len_exit = sqrt(nn); }
             }
         }
+        if (nxt < 0) len_exit = len_min;  /* a cell-sized length for the tests below */
+        /* degeneracy distance on this leg at the far end of this step */
+        const double tol_at = tau > 0.0 ? tau + err.e_pos + err.e_dir * (fabs(t1 < tmax ? t1 : tmax) + len_exit)
+                                        : -1.0;
         /* does the ray meet the sphere inside this cell? */
         int hit = 0;
-        double ts = HUGE_VAL;
+        double ts = HUGE_VAL, disc_hit = 1.0;
         if (E && bounces < E->max_bounces) {
             double disc;
             ts = sphere_hit(E, o, d, inside, &disc);
+            disc_hit = disc;
             /* near-grazing: the hit point's error grows as 1/sqrt(disc), so the
              * bent direction (and all that follows) is ill-conditioned */
-            if (fabs(disc) < 1e-2) R->degen = 1;
+            if (fabs(disc) < 1e-2) R->flags |= ORC_FLAG_BEND;
             hit = ts >= t0 && ts < t1 && ts < tmax;
-            if (isfinite(ts) && nxt >= 0) {
-                /* a hit next to the exit face: which cell it falls in is a tie */
+            if (isfinite(ts) && nxt >= 0 && tau > 0.0) {
+                /* a hit next to the exit face: which cell it falls in is a tie
+                 * (the FP32 hit parameter is off by ~1e-7 (|ts| + r / sqrt(disc))) */
                 double ps[3];
                 for (int a = 0; a < 3; ++a) ps[a] = o[a] + ts * d[a];
-                if (plane_dist(S, i, nxt, ps) < tau) R->degen = 1;
+                const double e_ts = 1e-7 * (fabs(ts) + E->r / sqrt(fabs(disc) > 1e-12 ? fabs(disc) : 1e-12));
+                if (plane_dist(S, i, nxt, ps) < tol_at + cos_exit * e_ts) R->flags |= ORC_FLAG_EDGE;
             }
         }
         const double tend = hit ? ts : t1;
@@ -405,16 +503,45 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
          * crossing's position gradient is ill-conditioned at FP32 */
         if (!hit && nxt >= 0 && t1 < tmax && tau > 0.0 &&
             (1e-7 * fabs(t1) + 0.1 * tau) > 1e-3 * cos_exit * len_exit)
-            R->degen = 1;
-        /* degeneracy test at the step's end point */
-        {
+            R->flags |= ORC_FLAG_GRAZE;
+        if (tau > 0.0) {
+            /* near a Voronoi edge or vertex: the step's end point within tol
+             * of another face plane of the cell ... */
             const double te = (hit || (nxt >= 0 && t1 < tmax)) ? tend : tmax;
             double p[3];
             for (int a = 0; a < 3; ++a) p[a] = o[a] + te * d[a];
             for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
                 const int64_t k = S->adj[f];
                 if (!hit && k == nxt && te == t1) continue;
-                if (plane_dist(S, i, k, p) < tau) { R->degen = 1; break; }
+                if (plane_dist(S, i, k, p) < tol_at) { R->flags |= ORC_FLAG_EDGE; break; }
+            }
+            /* ... or the ray within tol of the line where the plane it leaves
+             * by meets another face plane (near t_end a grazing exit plane
+             * stays close to the ray, so the line can be near the ray past
+             * the end point although the end point is not near the plane) */
+            if (!hit && !(R->flags & ORC_FLAG_EDGE)) {
+                double ne[3], he;
+                int64_t skip = -1;
+                int have = 0;
+                if (nxt >= 0 && t1 < tmax) {
+                    bisector_plane(S, i, nxt, ne, &he);
+                    skip = nxt;
+                    have = 1;
+                } else {
+                    /* the step ends on the scene box: the face whose slab gives tmax */
+                    for (int a = 0; a < 3 && !have; ++a) {
+                        if (d[a] == 0.0) continue;
+                        const double bnd = d[a] > 0.0 ? S->box[3 + a] : S->box[a];
+                        if (fabs((bnd - o[a]) / d[a] - tmax) <= 1e-12 * (1.0 + fabs(tmax))) {
+                            ne[0] = ne[1] = ne[2] = 0.0;
+                            ne[a] = d[a] > 0.0 ? 1.0 : -1.0;
+                            he = ne[a] * bnd;
+                            have = 1;
+                        }
+                    }
+                }
+                const double w0 = t0 - len_exit, w1 = te + len_exit;
+                if (have && near_edge(S, i, skip, ne, he, o, d, w0, w1, tol_at)) R->flags |= ORC_FLAG_EDGE;
             }
         }
         seg_t s;
@@ -448,8 +575,29 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
             /* bounce: the new ray starts at the hit point, in the same cell */
             double p[3], k;
             for (int a = 0; a < 3; ++a) p[a] = o[a] + ts * d[a];
-            if (sphere_bounce(E, p, d, inside, &k)) inside = !inside;
-            if (E->ior > 0.0 && fabs(k) < 1e-2) R->degen = 1;  /* near the critical angle */
+            const double eta = E->ior > 0.0 ? (inside ? E->ior : 1.0 / E->ior) : 0.0;
+            const int crossed = sphere_bounce(E, p, d, inside, &k);
+            if (crossed) inside = !inside;
+            if (E->ior > 0.0 && fabs(k) < 1e-2) R->flags |= ORC_FLAG_BEND;  /* near the critical angle */
+            /* error bound of the new leg: the FP32 hit point (its parameter
+             * carries ~1e-7 r / sqrt(disc)) and the normal through it; a
+             * reflection keeps the direction's error and adds up to 4 times the
+             * normal's, a refraction scales both by up to eta + eta^2 / sqrt(k)
+             * (taken twice for safety) */
+            {
+                double oc2 = 0.0;
+                for (int a = 0; a < 3; ++a) oc2 += (s.o[a] - E->c[a]) * (s.o[a] - E->c[a]);
+                const double dh = fabs(disc_hit) > 1e-12 ? fabs(disc_hit) : 1e-12;
+                const double e_p = err.e_pos + err.e_dir * ts + 1e-7 * (ts + sqrt(oc2) + E->r / sqrt(dh));
+                const double e_n = e_p / E->r;
+                if (crossed) {
+                    const double rk = 1.0 / sqrt(fabs(k) > 1e-12 ? fabs(k) : 1e-12);
+                    err.e_dir = 2.0 * (eta + eta * eta * rk) * (err.e_dir + e_n) + 1e-7 * (1.0 + rk);
+                } else {
+                    err.e_dir = err.e_dir + 4.0 * e_n + 1e-7;
+                }
+                err.e_pos = e_p;
+            }
             for (int a = 0; a < 3; ++a) o[a] = p[a];
             s_off += ts;
             t0 = 0.0;
@@ -462,7 +610,7 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
         if (t1 > t0) t0 = t1;
         i = nxt;
     }
-    if (T <= eps && fabs(T - eps) <= 1e-3 * eps) R->degen = 1;
+    if (T <= eps && fabs(T - eps) <= 1e-3 * eps) R->flags |= ORC_FLAG_STOP;
     for (int ch = 0; ch < 3; ++ch) R->rgb[ch] = C[ch];
     R->T = T;
     R->depth = D;
@@ -592,7 +740,8 @@ static int64_t ray_start(const scene_t *S, const double *cam, const cam_start_t 
 
 /*
  * Forward render of n_rays pixels of one camera (pixels == NULL: all pixels
- * in order).  Outputs per ray: rgb[3], trans, depth, steps, status, degen.
+ * in order).  Outputs per ray: rgb[3], trans, depth, steps, status, flags
+ * (ORC_FLAG_*).
  * Optional trace (max_trace > 0): cells visited and raw exit parameters,
  * row-major [n_rays, max_trace].  Returns 0, or -1 on bad arguments.
  */
@@ -601,7 +750,7 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
                const double *cam, int64_t n_rays, const int64_t *pixels,
                double eps, int max_steps, double tau,
                double *rgb, double *trans, double *depth, int32_t *steps, uint8_t *status,
-               uint8_t *degen, int max_trace, int32_t *trace_cells, double *trace_t,
+               uint8_t *flags, int max_trace, int32_t *trace_cells, double *trace_t,
                const double *effects, int n_threads)
 {
     scene_t S;
@@ -629,13 +778,13 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
             render_ray(&S, start, ro, rd, tmin, tmax, eps, max_steps, tau, Y, &R, NULL,
                        max_trace, tc, tt, EP);
         }
-        if (sdeg) R.degen = 1;
+        if (sdeg) R.flags |= ORC_FLAG_CAMERA;
         for (int ch = 0; ch < 3; ++ch) rgb[3 * r + ch] = R.rgb[ch];
         trans[r] = R.T;
         depth[r] = R.depth;
         if (steps) steps[r] = R.steps;
         if (status) status[r] = R.status;
-        if (degen) degen[r] = R.degen;
+        if (flags) flags[r] = R.flags;
     }
     return 0;
 }

@@ -57,13 +57,14 @@ def main():
         "# of Sec. 3.1 (density, SH, and positions through the segment widths) of",
         "# sum(g_rgb * rgb) + sum(g_trans * T) + sum(g_depth * depth) over the sampled pixels.",
         "# Written by tests/golden/make_golden.py, which calls only oracle/ and the input generators.",
-        "# pixel  g_r  g_g  g_b  g_T  g_depth  |  r  g  b  T  depth  steps  degenerate",
+        "# pixel  g_r  g_g  g_b  g_T  g_depth  |  r  g  b  T  depth  steps  flags",
+        "# (flags: near-degenerate classes, 1 edge/vertex tie, 2 camera tie, 4 stop tie, 8 grazing, 16 bend)",
     ]
     for k in range(len(px)):
         lines.append("px %d %r %r %r %r %r | %r %r %r %r %r %d %d" % (
             px[k], *map(float, g_rgb[k]), float(g_trans[k]), float(g_depth[k]),
             *map(float, f["rgb"][k]), float(f["trans"][k]), float(f["depth"][k]),
-            int(f["steps"][k]), int(f["degen"][k])))
+            int(f["steps"][k]), int(f["flags"][k])))
     lines.append("# site  d_sigma  d_sh(r, g, b)  d_pos(x, y, z)")
     for i in sites:
         lines.append("site %d %r %r %r %r %r %r %r" % (

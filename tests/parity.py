@@ -2,11 +2,17 @@
 
 Tolerances:
 
-* visited cells: bit-exact on every ray the oracle does not flag as
-  near-degenerate;
+* visited cells: bit-exact on every ray except those the oracle flags as
+  passing within tau of a Voronoi edge or vertex, or as starting within tau
+  of a bisector (``tie``); a ray whose transmittance meets eps within a
+  relative 1e-3 at a stop test (``stop_tie``) may end one step earlier or
+  later, with the shorter cell sequence a prefix of the longer;
 * images (rgb, transmittance, depth): RMSE <= 1e-5 over all rays;
 * gradients: ||g - g_ref||_2 / ||g_ref||_2 <= 1e-3 per tensor, with the loss
-  restricted to non-degenerate rays.
+  restricted to rays without any flag (grazing crossings and ill-conditioned
+  sphere bounces carry an FP32 conditioning error in the gradient only);
+* the flagged fraction of each class is bounded (``check_flag_fractions``),
+  so a classifier that flags too much cannot hollow out the comparisons.
 """
 import copy
 
@@ -64,21 +70,58 @@ def assert_images_close(g, o, rows=None, tol=IMG_RMSE):
     return err
 
 
+# Upper bounds on the fraction of rays in each near-degenerate class.  The
+# measured rates are far lower (edge ties ~0.1-1 %, grazing ~0.2-3 %, stop
+# ties ~0.1 %); a bound catches a classifier that flags far too much.
+FLAG_BOUNDS = {"edge": 0.03, "camera": 0.0, "stop": 0.01, "graze": 0.06, "bend": 0.10, "any": 0.10}
+
+
+def check_flag_fractions(flags, bounds=None):
+    """Per-class counts of the oracle's flags; asserts each fraction is within
+    its bound (``bounds`` overrides entries of FLAG_BOUNDS)."""
+    b = dict(FLAG_BOUNDS, **(bounds or {}))
+    c = oracle.flag_counts(flags)
+    n = max(c["rays"], 1)
+    for k, lim in b.items():
+        assert c[k] <= lim * n, f"{c[k]} of {n} rays flagged '{k}' (bound {lim:.0%}): {c}"
+    return c
+
+
+def assert_steps_match(steps_gpu, orc, rows=None):
+    """Cell-step counts equal on every ray that is not a tie; a stop tie may
+    differ by one step."""
+    g = np.asarray(steps_gpu if rows is None else steps_gpu[rows])
+    keep = ~orc["tie"] & ~orc["stop_tie"]
+    np.testing.assert_array_equal(g[keep], orc["steps"][keep])
+    st = orc["stop_tie"] & ~orc["tie"]
+    assert np.all(np.abs(g[st].astype(np.int64) - orc["steps"][st]) <= 1)
+
+
 def compare_traces(cells_gpu, counts_gpu, orc, max_per_ray):
-    """Number of mismatching non-degenerate rays and number of degenerate rays."""
-    deg = orc["degen"]
+    """Number of rays whose visited cells differ from the oracle's where they
+    must not, and the number of tie rays left out.  Grazing and bend rays are
+    compared bit for bit like any other; a stop tie may end one step apart."""
+    tie = orc["tie"]
+    stop = orc["stop_tie"]
     bad = 0
-    for r in range(len(deg)):
-        if deg[r]:
+    for r in range(len(tie)):
+        if tie[r]:
             continue
         n = int(orc["steps"][r])
-        if int(counts_gpu[r]) != n:
-            bad += 1
-            continue
-        m = min(n, max_per_ray)
+        ng = int(counts_gpu[r])
+        if stop[r]:
+            if abs(ng - n) > 1:
+                bad += 1
+                continue
+            m = min(n, ng, max_per_ray)
+        else:
+            if ng != n:
+                bad += 1
+                continue
+            m = min(n, max_per_ray)
         if not np.array_equal(cells_gpu[r, :m], orc["trace_cells"][r, :m]):
             bad += 1
-    return bad, int(deg.sum())
+    return bad, int(tie.sum())
 
 
 def rel_l2(a, b):

@@ -10,7 +10,8 @@ from paper_2502_01157_gb300 import rf
 from paper_2502_01157_gb300 import scenes as S
 from tests.helpers import camera_at, random_scene
 from tests.parity import (GRAD_REL, assert_images_close, compare_traces, foam_of, gpu_render,
-                          rel_l2, rounded_scene)
+                          rel_l2, rounded_scene, assert_steps_match,
+                          check_flag_fractions)
 
 pytestmark = pytest.mark.gpu
 
@@ -58,10 +59,10 @@ def test_camera_models_match_oracle(dt, deg):
     def check(cam, sl):
         o = oracle.render(ref, cam, trace=512)
         err = assert_images_close({k: v[sl] for k, v in g.items()}, o)
-        ok = ~o["degen"]
-        np.testing.assert_array_equal(g["steps"][sl][ok], o["steps"][ok])
+        assert_steps_match(g["steps"][sl], o)
+        nd = check_flag_fractions(o["flags"])
         cells, counts = foam.trace(cam, max_per_ray=512)
-        bad, nd = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 512)
+        bad, _ = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 512)
         print(f"{dt} deg {deg} model {cam.model} shutter {cam.shutter}: {err}, degenerate {nd}")
         assert bad == 0
 
@@ -80,6 +81,7 @@ def _sphere_cams():
                   shutter=(0.1, 0.0, 0.2))]
 
 
+SPHERE_FLAG_BOUNDS = {"edge": 0.07, "bend": 0.05, "any": 0.10}
 SPHERES = {"mirror": S.Sphere((0.1, 0.0, 0.05), 0.35, ior=0.0, max_bounces=4),
            "glass": S.Sphere((0.1, 0.0, 0.05), 0.35, ior=1.5, max_bounces=6),
            "dense glass": S.Sphere((0.1, 0.0, 0.05), 0.45, ior=2.4, max_bounces=3),
@@ -109,10 +111,12 @@ def test_sphere_forward_and_backward_match_oracle(name, dt, deg):
     def check(cam, sl):
         o = oracle.render(ref, cam, trace=512, effects=sph)
         err = assert_images_close({k: v[sl] for k, v in g.items()}, o)
-        ok = ~o["degen"]
-        np.testing.assert_array_equal(g["steps"][sl][ok], o["steps"][ok])
+        assert_steps_match(g["steps"][sl], o)
+        # the bent rays' FP32 error grows with each refraction: edge ties are
+        # measured with it and run to a few per cent behind dense glass
+        nd = check_flag_fractions(o["flags"], SPHERE_FLAG_BOUNDS)
         cells, counts = foam.trace(cam, max_per_ray=512, effects=sph)
-        bad, nd = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 512)
+        bad, _ = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 512)
         straight = oracle.render(ref, cam)
         n_bounced[0] += int(np.sum(np.abs(straight["trans"] - o["trans"]) > 1e-6))
         print(f"{name} {dt} deg {deg} cam {cam.model}: {err}, degenerate {nd}, traces bad {bad}")
@@ -235,7 +239,7 @@ def test_full_size_c3_fisheye_rolling_shutter_glass_sphere_sampled():
     o = oracle.render(sc, cam, pixels=px, effects=sph)
     g = {k: out[k].cpu().numpy()[px] for k in ("rgb", "trans", "depth")}
     err = assert_images_close(g, o)
-    print(f"c3 fisheye + shutter + glass: {err}, degenerate {int(o['degen'].sum())}")
+    print(f"c3 fisheye + shutter + glass: {err}, flags {check_flag_fractions(o['flags'], SPHERE_FLAG_BOUNDS)}")
     keep = px[~o["degen"]]
     gr = np.zeros((cam.n_rays, 3), np.float32)
     gr[keep] = rng.normal(size=(len(keep), 3))

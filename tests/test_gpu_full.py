@@ -10,11 +10,12 @@ import oracle
 from paper_2502_01157_gb300 import rf
 from paper_2502_01157_gb300 import scenes as S
 from tests.helpers import random_scene
-from tests.parity import (GRAD_REL, assert_images_close, compare_traces, foam_of, gpu_render,
-                          rel_l2, rounded_scene)
+from tests.parity import (GRAD_REL, assert_images_close, assert_steps_match, check_flag_fractions,
+                          compare_traces, foam_of, gpu_render, rel_l2, rounded_scene)
 
 pytestmark = pytest.mark.gpu
 N_SAMPLE = 1500
+RECORD = 384   # walk-record steps of the timed training step
 
 
 def window(cam, x0, y0, w, h):
@@ -28,38 +29,38 @@ def _check_forward_sampled(scene, foam, cams, dt="f32", seed=0):
     ref = rounded_scene(scene, dt)
     rng = np.random.default_rng(seed)
     base = 0
-    n_deg = 0
+    flags = []
     for cam in cams:
         px = np.sort(rng.choice(cam.n_rays, size=min(N_SAMPLE, cam.n_rays), replace=False))
         o = oracle.render(ref, cam, pixels=px)
         rows = base + px
         err = assert_images_close(g, o, rows)
-        keep = ~o["degen"]
-        np.testing.assert_array_equal(g["steps"][rows][keep], o["steps"][keep])
-        n_deg += int(o["degen"].sum())
+        assert_steps_match(g["steps"], o, rows)
+        flags.append(o["flags"])
         base += cam.n_rays
-    return g, err, n_deg
+    return g, err, check_flag_fractions(np.concatenate(flags))
 
 
 def _check_traces(scene, foam, cam, dt="f32"):
     ref = rounded_scene(scene, dt)
     bad_total = 0
-    deg_total = 0
+    flags = []
     for (x0, y0) in [(0, 0), (cam.width // 2 - 16, cam.height // 2 - 8), (cam.width - 32, cam.height - 16)]:
         win = window(cam, max(0, x0), max(0, y0), 32, 16)
         cells, counts = foam.trace(win, max_per_ray=1024)
         o = oracle.render(ref, win, trace=1024)
-        bad, ndeg = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 1024)
+        bad, _ = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 1024)
         bad_total += bad
-        deg_total += ndeg
-    return bad_total, deg_total
+        flags.append(o["flags"])
+    return bad_total, check_flag_fractions(np.concatenate(flags))
 
 
-def _check_backward_sampled(scene, foam, cams, dt="f32", seed=1):
-    """Full launch; the loss weights only sampled, non-degenerate rays, so the
-    oracle can compute the reference gradient."""
+def _check_backward_sampled(scene, foam, cams, dt="f32", seed=1, record=0):
+    """Full launch; the loss weights only sampled, unflagged rays, so the
+    oracle can compute the reference gradient.  ``record`` > 0: the backward
+    replays the forward's walk record, as the timed training step does."""
     ref = rounded_scene(scene, dt)
-    fwd = foam.render(cams)
+    fwd = foam.render(cams, record=record)
     R = rf.n_rays_of(cams)
     rng = np.random.default_rng(seed)
     gr = np.zeros((R, 3), np.float32)
@@ -101,10 +102,10 @@ def test_c2_full_forward_backward(c2):
     foam = foam_of(c2)
     g, err, nd = _check_forward_sampled(c2, foam, cams)
     bad, ndeg = _check_traces(c2, foam, cams[0])
-    print(f"c2: image err {err}, degenerate {nd}/{N_SAMPLE} sampled, traces {bad} bad / {ndeg} degenerate")
+    print(f"c2: image err {err}, flags (sampled) {nd}, traces {bad} bad, flags (windows) {ndeg}")
     assert bad == 0
-    errs = _check_backward_sampled(c2, foam, cams)
-    print("c2 grads", errs)
+    errs = _check_backward_sampled(c2, foam, cams, record=RECORD)
+    print("c2 grads (replayed record)", errs)
     for k, e in errs.items():
         assert e <= GRAD_REL, f"{k}: {e:.2e}"
 
@@ -115,10 +116,10 @@ def test_c3_full_forward_backward(c3, dt):
     foam = foam_of(c3, dt)
     g, err, nd = _check_forward_sampled(c3, foam, cams, dt)
     bad, ndeg = _check_traces(c3, foam, cams[0], dt)
-    print(f"c3 {dt}: image err {err}, degenerate {nd}, traces {bad} bad / {ndeg} degenerate")
+    print(f"c3 {dt}: image err {err}, flags (sampled) {nd}, traces {bad} bad, flags (windows) {ndeg}")
     assert bad == 0
-    errs = _check_backward_sampled(c3, foam, cams, dt)
-    print(f"c3 {dt} grads", errs)
+    errs = _check_backward_sampled(c3, foam, cams, dt, record=RECORD)
+    print(f"c3 {dt} grads (replayed record)", errs)
     for k, e in errs.items():
         assert e <= GRAD_REL, f"{k}: {e:.2e}"
     if dt != "f32":
@@ -133,8 +134,8 @@ def test_c4_eight_mixed_cameras_one_launch(c4):
     assert len(cams) == 8 and rf.n_rays_of(cams) == 9_484_800
     foam = foam_of(c4)
     g, err, nd = _check_forward_sampled(c4, foam, cams)
-    print(f"c4: image err {err}, degenerate {nd}")
-    errs = _check_backward_sampled(c4, foam, cams)
+    print(f"c4: image err {err}, flags {nd}")
+    errs = _check_backward_sampled(c4, foam, cams, record=RECORD)
     print("c4 grads", errs)
     for k, e in errs.items():
         assert e <= GRAD_REL, f"{k}: {e:.2e}"

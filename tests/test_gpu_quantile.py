@@ -9,7 +9,7 @@ import oracle
 from paper_2502_01157_gb300 import rf
 from paper_2502_01157_gb300 import scenes as S
 from tests.helpers import camera_at, random_scene
-from tests.parity import GRAD_REL, foam_of, rel_l2, rounded_scene
+from tests.parity import GRAD_REL, check_flag_fractions, foam_of, rel_l2, rounded_scene
 
 pytestmark = pytest.mark.gpu
 Q_RMSE = 1e-5
@@ -54,6 +54,7 @@ def test_quantile_forward_and_backward_match_oracle(deg, dt, scale):
         print(f"deg {deg} {dt} x{scale}: quantile rmse {err:.2e}, max rel {rel:.2e}, mean {qo.mean():.3f}")
         assert err <= Q_RMSE
         o = oracle.render(ref, cam)
+        check_flag_fractions(o["flags"])
         gq[sl][o["degen"]] = 0
         gr[sl][o["degen"]] = 0
         G = oracle.render_bwd(ref, cam, gr[sl], g_quantile=gq[sl])
