@@ -928,7 +928,7 @@ RF_API rf_status rf_adjacency_build(rf_adjacency *a, int64_t n, const float *pos
     //    grown by 5% of its extent (at least 1e-3) on every side
     const int32_t init[7] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN, 0};
     RF_CUDA(cudaMemcpyAsync(a->bbox, init, sizeof init, cudaMemcpyHostToDevice, st));
-    bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(pos, n, a->bbox, a->bbox + 6);
+    bbox_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, grid_cap(8)), 256, 0, st>>>(pos, n, a->bbox, a->bbox + 6);
     RF_CUDA(cudaGetLastError());
     RF_CUDA(cudaMemcpyAsync(a->host, a->bbox, sizeof init, cudaMemcpyDeviceToHost, st));
     RF_CUDA(cudaStreamSynchronize(st));
@@ -1007,14 +1007,14 @@ RF_API rf_status rf_adjacency_build(rf_adjacency *a, int64_t n, const float *pos
         P.edge_cap = (int32_t)std::min<int64_t>(a->edge_cap, INT32_MAX);
         P.counters = a->counters;
         P.wide_list = a->wide;
-        const int64_t blocks = std::min<int64_t>((n + kWarps - 1) / kWarps, 152 * 256);
+        const int64_t blocks = std::min<int64_t>((n + kWarps - 1) / kWarps, grid_cap(256));
         cell_kernel<kMaxPlanes, kWarps, 7><<<(unsigned)blocks, 32 * kWarps, 0, st>>>(P);
         RF_CUDA(cudaGetLastError());
         // the cells that overflowed, again with room for more faces
         P.site_list = a->wide;
         P.n_list = a->counters + 1;
         P.wide_list = nullptr;
-        cell_kernel<kWideMaxPlanes, kWideWarps, 1><<<152 * 8, 32 * kWideWarps, 0, st>>>(P);
+        cell_kernel<kWideMaxPlanes, kWideWarps, 1><<<grid_cap(8), 32 * kWideWarps, 0, st>>>(P);
         RF_CUDA(cudaGetLastError());
         RF_CUDA(cudaMemcpyAsync(a->host, a->counters, sizeof(int32_t) * 8, cudaMemcpyDeviceToHost, st));
         RF_CUDA(cudaStreamSynchronize(st));

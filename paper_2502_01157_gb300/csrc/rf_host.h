@@ -37,6 +37,10 @@ namespace rf {
 rf_status fail(rf_status code, const char *fmt, ...);
 rf_status cuda_fail(cudaError_t e, const char *what);
 
+// per_sm x the current device's SM count (queried once per device), the cap
+// of the grid-stride kernels' grids
+int grid_cap(int per_sm);
+
 #define RF_CUDA(expr)                                                  \
     do {                                                               \
         cudaError_t e_ = (expr);                                       \

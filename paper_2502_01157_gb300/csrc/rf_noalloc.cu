@@ -92,9 +92,10 @@ __global__ void raw_nearest_site_kernel(const float *__restrict__ pos, int64_t n
 }
 
 // Alg. 1 per ray on the caller's CSR arrays; the face record of (i, j) is
-// formed on the fly exactly as the packer forms it.  Out-of-range offsets or
-// neighbour ids end the ray (status RF_RAY_MAX_STEPS) instead of reading
-// outside the arrays.
+// formed on the fly exactly as the packer forms it.  An out-of-range offset
+// ends the ray there and an out-of-range neighbour id is skipped, instead of
+// being read; this entry point has no per-ray status output, so a malformed
+// adjacency silently truncates the affected rays.
 template <typename AT, int DEG>
 __global__ void __launch_bounds__(kBlock) raw_fwd_kernel(const RawParams p, float *rgb, float *trans,
                                                          float *depth) {
@@ -256,7 +257,7 @@ RF_API rf_status rf_render_fwd_noalloc(int64_t n_sites, int64_t n_edges, const f
             prm.o[c][2] = cams[first + c].c2w[11];
         }
         int64_t blocks = (n_sites + 255) / 256;
-        if (blocks > 152 * 8) blocks = 152 * 8;
+        if (blocks > grid_cap(8)) blocks = grid_cap(8);
         raw_nearest_site_kernel<<<dim3((unsigned)blocks, count), 256, 0, st>>>(pos, n_sites, prm, keys + first);
         RF_CUDA(cudaGetLastError());
         const int64_t tiles = make_launch_cams(cams, first, count, ray_begin, &p.lc);

@@ -245,7 +245,7 @@ RF_API rf_status rf_render_bwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_
         RF_CUDA(cudaGetLastError());
     }
     if (acc) {
-        const int64_t blocks = std::min<int64_t>((s->n_sites + 255) / 256, 152 * 8);
+        const int64_t blocks = std::min<int64_t>((s->n_sites + 255) / 256, grid_cap(8));
         add_site_grads_kernel<<<(unsigned)blocks, 256, 0, st>>>(acc, s->n_sites, gr->pos, gr->density);
         RF_CUDA(cudaGetLastError());
     }
@@ -267,7 +267,7 @@ RF_API rf_status rf_mse_grad(const float *rgb, const float *target, int64_t n, f
     if (!rgb || !target || !d_rgb || n < 0) return fail(RF_ERR_INVALID_ARG, "bad mse arguments");
     if (n == 0) return RF_OK;
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > grid_cap(8)) blocks = grid_cap(8);
     mse_grad_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(rgb, target, n, scale, d_rgb, loss);
     RF_CUDA(cudaGetLastError());
     return RF_OK;

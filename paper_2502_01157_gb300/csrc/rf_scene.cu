@@ -1,5 +1,6 @@
 // rf_scene.cu -- scene packing, validation, scene box and nn(o) for the
 // Radiant Foam renderer (arXiv 2502.01157), sm_103a.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -25,6 +26,19 @@ rf_status fail(rf_status code, const char *fmt, ...) {
 rf_status cuda_fail(cudaError_t e, const char *what) {
     return fail(e == cudaErrorMemoryAllocation ? RF_ERR_OOM : RF_ERR_CUDA, "%s: %s (%s)", what,
                 cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+int grid_cap(int per_sm) {
+    static std::atomic<int> cached[64] = {};
+    int dev = 0;
+    int sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        sms = cached[dev].load(std::memory_order_relaxed);
+        if (sms <= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            cached[dev].store(sms, std::memory_order_relaxed);
+    }
+    if (sms <= 0) sms = 152;  // the attribute query failed: a GB300's count
+    return sms * per_sm;
 }
 
 SceneDev scene_dev(const rf_scene *s) {
@@ -284,7 +298,7 @@ rf_status launch_nearest_sites(const rf_scene *s, const rf_camera *cams, int n,
     RF_CUDA(cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * n, st));
     const int threads = 256;
     int64_t blocks = (s->n_sites + threads - 1) / threads;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > grid_cap(8)) blocks = grid_cap(8);
     nearest_site_kernel<<<dim3((unsigned)blocks, n), threads, 0, st>>>(s->cells, s->n_sites, prm, keys);
     RF_CUDA(cudaGetLastError());
     return RF_OK;
@@ -433,7 +447,7 @@ RF_API rf_status rf_scene_create(const rf_scene_desc *desc, void *stream, rf_sce
         if ((ce = cudaMemcpyAsync(s->flags, init, sizeof init, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return bail(cuda_fail(ce, "box init"));
         int64_t blocks = (n + threads - 1) / threads;
-        if (blocks > 152 * 4) blocks = 152 * 4;
+        if (blocks > grid_cap(4)) blocks = grid_cap(4);
         box_kernel<<<(unsigned)blocks, threads, 0, st>>>(desc->pos, n, s->flags);
         if ((ce = cudaMemcpyAsync(keys, s->flags, sizeof keys, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (ce = cudaStreamSynchronize(st)) != cudaSuccess)

@@ -264,6 +264,7 @@ class Foam:
     def __init__(self, pos, adj_off, adj_idx, density, sh, aabb=None, stream=None):
         self.pos = pos.contiguous()
         self._aabb = aabb
+        self._topology = 0     # bumped when the neighbour lists are replaced
         self._attrs(density, sh)
         self._create(adj_off, adj_idx, stream)
 
@@ -292,6 +293,7 @@ class Foam:
         _check(L.rf_scene_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
         self._h = h
         self._pos_version = self.pos._version
+        self._topology = getattr(self, "_topology", 0) + 1
 
     def _attrs(self, density, sh):
         if density.dtype not in _DTYPES or sh.dtype != density.dtype:
@@ -359,6 +361,12 @@ class Foam:
         _check(lib().rf_scene_info(self.handle, ctypes.byref(n), ctypes.byref(e), box,
                                    ctypes.byref(b)))
         return dict(n_sites=n.value, n_edges=e.value, aabb=list(box), device_bytes=b.value)
+
+    def state(self):
+        """What a render reads from this foam: the adjacency generation and
+        the attribute / position tensors with their in-place versions."""
+        return (self._topology, self.density, self.sh, self.pos,
+                (self.density._version, self.sh._version, self.pos._version))
 
     def set_attributes(self, density, sh):
         self._attrs(density, sh)
@@ -568,6 +576,48 @@ def render_noalloc(pos, adj_off, adj_idx, density, sh, aabb, cams, eps: float = 
     return out
 
 
+class _scene_as_rendered:
+    """Context manager for a backward: puts the foam back into the state its
+    forward rendered (another render may have swapped the attribute tensors
+    or moved the sites since, e.g. with gradient accumulation over several
+    renders) and restores the newer state afterwards.  Attributes or
+    positions edited in place, or replaced neighbour lists, cannot be undone:
+    that raises instead of returning wrong gradients."""
+
+    def __init__(self, foam, state):
+        self.foam = foam
+        self.topo, self.density, self.sh, self.pos, self.versions = state
+        self.swapped = None
+
+    def __enter__(self):
+        f = self.foam
+        if f._topology != self.topo:
+            raise RuntimeError("the foam's adjacency was rebuilt between this render and its backward")
+        if (self.density._version, self.sh._version, self.pos._version) != self.versions:
+            raise RuntimeError("density, sh or positions were modified in place between this render "
+                               "and its backward")
+        cur = (f.density, f.sh, f.pos)
+        if cur[0] is self.density and cur[1] is self.sh and cur[2] is self.pos \
+                and f._pos_version == self.pos._version:
+            return self
+        self.swapped = cur
+        if cur[0] is not self.density or cur[1] is not self.sh:
+            f.set_attributes(self.density, self.sh)
+        if cur[2] is not self.pos or f._pos_version != self.pos._version:
+            f.update_positions(self.pos)
+        return self
+
+    def __exit__(self, *exc):
+        if self.swapped is not None:
+            d, s, p = self.swapped
+            f = self.foam
+            if f.density is not d or f.sh is not s:
+                f.set_attributes(d, s)
+            if f.pos is not p:
+                f.update_positions(p)
+        return False
+
+
 class _Render(torch.autograd.Function):
     @staticmethod
     def forward(ctx, foam, cams, eps, max_steps, quantile, effects, record, density, sh, pos):
@@ -575,6 +625,7 @@ class _Render(torch.autograd.Function):
         out = foam.render(cams, eps=eps, max_steps=max_steps, quantile=quantile, effects=effects,
                           record=record)
         ctx.walk_record = out.get("walk_record")
+        ctx.foam_state = foam.state()
         ctx.foam, ctx.cams, ctx.eps, ctx.max_steps, ctx.quantile = foam, cams, eps, max_steps, quantile
         ctx.effects = effects
         ctx.dtypes = (density.dtype, sh.dtype)
@@ -605,11 +656,12 @@ class _Render(torch.autograd.Function):
                 fwd["quantile_aux"] = saved[3]
             if ctx.walk_record is not None:
                 fwd["walk_record"] = ctx.walk_record
-            foam.backward(ctx.cams, fwd,
-                          z(g_rgb) if g_rgb is not None else torch.zeros_like(rgb),
-                          z(g_trans), z(g_depth), grads=grads, eps=ctx.eps,
-                          max_steps=ctx.max_steps, d_quantile=z(g_quant) if ctx.quantile else None,
-                          effects=ctx.effects)
+            with _scene_as_rendered(foam, ctx.foam_state):
+                foam.backward(ctx.cams, fwd,
+                              z(g_rgb) if g_rgb is not None else torch.zeros_like(rgb),
+                              z(g_trans), z(g_depth), grads=grads, eps=ctx.eps,
+                              max_steps=ctx.max_steps, d_quantile=z(g_quant) if ctx.quantile else None,
+                              effects=ctx.effects)
         gd = grads.get("density")
         gs = grads.get("sh")
         ctx.walk_record = None
