@@ -367,48 +367,45 @@ static double plane_dist(const scene_t *S, int64_t i, int64_t k, const double *p
     return fabs(n[0] * p[0] + n[1] * p[1] + n[2] * p[2] - h);
 }
 
-/* Distance from the ray piece x(t) = o + t d, t in [w0, w1], to the line
- * where the planes {na.x = ha} and {nb.x = hb} (unit normals) meet: the
- * Voronoi edge of the three sites whose bisectors they are.  With the signed
- * distances s_a(t) = na.x(t) - ha and s_b(t) likewise, and g = na.nb, a
- * point's squared distance to that line is (s_a^2 + s_b^2 - 2 g s_a s_b) /
- * (1 - g^2), a convex quadratic in t; its minimum over [w0, w1] is taken at
- * the clamped stationary point.  Parallel planes have no line: HUGE_VAL. */
-static double ray_line_dist(const double *na, double ha, const double *nb, double hb,
-                            const double *o, const double *d, double w0, double w1)
+/* Distance between the ray's line x(t) = o + t d and the line where two
+ * planes it crosses meet (unit normals na, nb; ca = na.d and cb = nb.d its
+ * cosines to them, both > 0; it crosses them at ta and tb).  The signed
+ * distances to the planes are s_a = ca (t - ta) and s_b = cb (t - tb), a
+ * point's squared distance to the line is (s_a^2 + s_b^2 - 2 g s_a s_b) /
+ * (1 - g^2) with g = na.nb, and its minimum over t is
+ * (tb - ta)^2 ca^2 cb^2 / |cb na - ca nb|^2. */
+static double ray_line_dist(const double *na, double ca, double ta, const double *nb, double cb,
+                            double tb)
 {
-    const double g = na[0] * nb[0] + na[1] * nb[1] + na[2] * nb[2];
-    const double s2 = 1.0 - g * g;
-    if (!(s2 > 1e-24)) return HUGE_VAL;
-    double aa = -ha, ab = -hb, ca = 0.0, cb = 0.0;
+    double w2 = 0.0;
     for (int k = 0; k < 3; ++k) {
-        aa += na[k] * o[k];
-        ab += nb[k] * o[k];
-        ca += na[k] * d[k];
-        cb += nb[k] * d[k];
+        const double w = cb * na[k] - ca * nb[k];
+        w2 += w * w;
     }
-    const double A = ca * ca + cb * cb - 2.0 * g * ca * cb;
-    const double B = aa * ca + ab * cb - g * (aa * cb + ab * ca);
-    double t = A > 0.0 ? -B / A : w0;
-    if (t < w0) t = w0;
-    if (t > w1) t = w1;
-    const double sa = aa + ca * t, sb = ab + cb * t;
-    const double q = (sa * sa + sb * sb - 2.0 * g * sa * sb) / s2;
-    return q > 0.0 ? sqrt(q) : 0.0;
+    if (!(w2 > 0.0)) return HUGE_VAL;  /* the same plane */
+    return fabs(tb - ta) * ca * cb / sqrt(w2);
 }
 
-/* Is a Voronoi edge of cell i within tol of the ray piece [w0, w1]?  The
- * step ends on the plane {ne.x = he} (the exit face `skip`, or a face of the
- * scene box); every other face plane k of the cell meets it in a line. */
-static int near_edge(const scene_t *S, int64_t i, int64_t skip, const double *ne, double he,
-                     const double *o, const double *d, double w0, double w1, double tol)
+/* Is the ray within tol of the Voronoi edge where the plane it leaves the
+ * cell by ({ne.x = he}, crossed at te: the exit face `skip` or a face of the
+ * scene box) meets the plane of another exit candidate (a front-facing face
+ * of cell i)?  Those two are the candidates whose order at FP32 decides the
+ * next cell; a grazing candidate keeps the ray near the edge although the
+ * crossing points lie apart. */
+static int near_edge(const scene_t *S, int64_t i, int64_t skip, const double *ne, double te,
+                     const double *o, const double *d, double tol)
 {
+    const double ce = ne[0] * d[0] + ne[1] * d[1] + ne[2] * d[2];
+    if (!(ce > 0.0)) return 0;
     for (int64_t f = S->off[i]; f < S->off[i + 1]; ++f) {
         const int64_t k = S->adj[f];
         if (k == skip) continue;
         double nk[3], hk;
         bisector_plane(S, i, k, nk, &hk);
-        if (ray_line_dist(ne, he, nk, hk, o, d, w0, w1) < tol) return 1;
+        const double ck = nk[0] * d[0] + nk[1] * d[1] + nk[2] * d[2];
+        if (!(ck > 0.0)) continue;
+        const double tk = (hk - (nk[0] * o[0] + nk[1] * o[1] + nk[2] * o[2])) / ck;
+        if (ray_line_dist(ne, ce, te, nk, ck, tk) < tol) return 1;
     }
     return 0;
 }
@@ -515,10 +512,8 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
                 if (!hit && k == nxt && te == t1) continue;
                 if (plane_dist(S, i, k, p) < tol_at) { R->flags |= ORC_FLAG_EDGE; break; }
             }
-            /* ... or the ray within tol of the line where the plane it leaves
-             * by meets another face plane (near t_end a grazing exit plane
-             * stays close to the ray, so the line can be near the ray past
-             * the end point although the end point is not near the plane) */
+            /* ... or the ray within tol of the edge between the plane it
+             * leaves by and another exit candidate */
             if (!hit && !(R->flags & ORC_FLAG_EDGE)) {
                 double ne[3], he;
                 int64_t skip = -1;
@@ -535,13 +530,11 @@ static void render_ray(const scene_t *S, int64_t start, const double *o_in, cons
                         if (fabs((bnd - o[a]) / d[a] - tmax) <= 1e-12 * (1.0 + fabs(tmax))) {
                             ne[0] = ne[1] = ne[2] = 0.0;
                             ne[a] = d[a] > 0.0 ? 1.0 : -1.0;
-                            he = ne[a] * bnd;
                             have = 1;
                         }
                     }
                 }
-                const double w0 = t0 - len_exit, w1 = te + len_exit;
-                if (have && near_edge(S, i, skip, ne, he, o, d, w0, w1, tol_at)) R->flags |= ORC_FLAG_EDGE;
+                if (have && near_edge(S, i, skip, ne, te, o, d, tol_at)) R->flags |= ORC_FLAG_EDGE;
             }
         }
         seg_t s;

@@ -239,7 +239,8 @@ def test_full_size_c3_fisheye_rolling_shutter_glass_sphere_sampled():
     o = oracle.render(sc, cam, pixels=px, effects=sph)
     g = {k: out[k].cpu().numpy()[px] for k in ("rgb", "trans", "depth")}
     err = assert_images_close(g, o)
-    print(f"c3 fisheye + shutter + glass: {err}, flags {check_flag_fractions(o['flags'], SPHERE_FLAG_BOUNDS)}")
+    cnt = check_flag_fractions(o["flags"], {"edge": 0.10, "bend": 0.05, "any": 0.15})
+    print(f"c3 fisheye + shutter + glass: {err}, flags {cnt}")
     keep = px[~o["degen"]]
     gr = np.zeros((cam.n_rays, 3), np.float32)
     gr[keep] = rng.normal(size=(len(keep), 3))

@@ -10,8 +10,8 @@ import oracle
 from paper_2502_01157_gb300 import rf
 from paper_2502_01157_gb300 import scenes as S
 from tests.helpers import random_scene
-from tests.parity import (GRAD_REL, assert_images_close, assert_steps_match, check_flag_fractions,
-                          compare_traces, foam_of, gpu_render, rel_l2, rounded_scene)
+from tests.parity import (FULL_SIZE_FLAG_BOUNDS, GRAD_REL, assert_images_close, assert_steps_match,
+                          check_flag_fractions, compare_traces, foam_of, gpu_render, rel_l2, rounded_scene)
 
 pytestmark = pytest.mark.gpu
 N_SAMPLE = 1500
@@ -38,7 +38,7 @@ def _check_forward_sampled(scene, foam, cams, dt="f32", seed=0):
         assert_steps_match(g["steps"], o, rows)
         flags.append(o["flags"])
         base += cam.n_rays
-    return g, err, check_flag_fractions(np.concatenate(flags))
+    return g, err, check_flag_fractions(np.concatenate(flags), FULL_SIZE_FLAG_BOUNDS)
 
 
 def _check_traces(scene, foam, cam, dt="f32"):
@@ -52,7 +52,7 @@ def _check_traces(scene, foam, cam, dt="f32"):
         bad, _ = compare_traces(cells.cpu().numpy(), counts.cpu().numpy(), o, 1024)
         bad_total += bad
         flags.append(o["flags"])
-    return bad_total, check_flag_fractions(np.concatenate(flags))
+    return bad_total, check_flag_fractions(np.concatenate(flags), FULL_SIZE_FLAG_BOUNDS)
 
 
 def _check_backward_sampled(scene, foam, cams, dt="f32", seed=1, record=0):
