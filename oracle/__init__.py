@@ -90,17 +90,19 @@ def lib():
             L.orc_camera_ray.restype = None
             L.orc_nearest_site.argtypes = [ctypes.c_int64, _d, _d, _d]
             L.orc_nearest_site.restype = ctypes.c_int64
+            L.orc_camera_start.argtypes = [ctypes.c_int64, _d, _d, _d]
+            L.orc_camera_start.restype = None
             L.orc_render.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int, _d,
                                      _d, ctypes.c_int64, _i64, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_double, _d, _d, _d, _i32, _u8, _u8, ctypes.c_int,
-                                     _i32, _d, _d, ctypes.c_int]
+                                     _i32, _d, _d, _d, ctypes.c_int]
             L.orc_render.restype = ctypes.c_int
             L.orc_render_bwd.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int, _d,
                                          _d, ctypes.c_int64, _i64, ctypes.c_double, ctypes.c_int,
-                                         _d, _d, _d, _d, _d, _d, _d, _d, ctypes.c_int]
+                                         _d, _d, _d, _d, _d, _d, _d, _d, _d, ctypes.c_int]
             L.orc_render_quantile.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d, _d, ctypes.c_int,
                                               _d, _d, ctypes.c_int64, _i64, ctypes.c_double,
-                                              ctypes.c_int, _d, _d, ctypes.c_int]
+                                              ctypes.c_int, _d, _d, _d, ctypes.c_int]
             L.orc_render_quantile.restype = ctypes.c_int
             L.orc_render_bwd.restype = ctypes.c_int
             L.orc_voronoi_faces.argtypes = [ctypes.c_int64, _d, ctypes.c_int64, _i64, _i64, _i64, _d,
@@ -148,6 +150,8 @@ def default_tau(scene, cam) -> float:
 
 
 class _SceneF64:
+    """FP64 copies of a scene's arrays in the layout the C code reads."""
+
     def __init__(self, scene):
         self.n = int(len(scene.pos))
         self.pos = _f64(scene.pos).reshape(-1)
@@ -158,6 +162,41 @@ class _SceneF64:
         self.deg = int(scene.sh_degree)
         self.box = _f64(np.concatenate([np.asarray(scene.aabb_min, np.float64).reshape(3),
                                         np.asarray(scene.aabb_max, np.float64).reshape(3)]))
+
+
+class Prepared:
+    """A scene converted to FP64 once, for many oracle calls on it (the
+    conversion of a 3M-site scene's SH rows takes longer than rendering a
+    few thousand rays).  The start cell nn(o) of each camera centre is also
+    found once and kept.  Pass it wherever a scene is expected."""
+
+    def __init__(self, scene):
+        self.f64 = _SceneF64(scene)
+        self.aabb_min = np.asarray(scene.aabb_min)
+        self.aabb_max = np.asarray(scene.aabb_max)
+        self.n_sites = self.f64.n
+        self.sh_degree = self.f64.deg
+        self._starts = {}
+
+    def start_info(self, cam) -> np.ndarray:
+        c = _cam(cam)
+        key = c[:12].tobytes()
+        if key not in self._starts:
+            out = np.zeros(2)
+            lib().orc_camera_start(self.f64.n, _p(self.f64.pos, _d), _p(c, _d), _p(out, _d))
+            self._starts[key] = out
+        return self._starts[key]
+
+
+def prepare(scene) -> Prepared:
+    return scene if isinstance(scene, Prepared) else Prepared(scene)
+
+
+def _scene_args(scene, cam):
+    """(FP64 scene, start info or None) for a scene or a Prepared one."""
+    if isinstance(scene, Prepared):
+        return scene.f64, scene.start_info(cam)
+    return _SceneF64(scene), None
 
 
 def sh_basis(degree: int, dirs) -> np.ndarray:
@@ -201,7 +240,7 @@ def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
     (STOP: the walk may end one step earlier or later) and ``degen`` (any
     flag: the gradient may carry the conditioning error)."""
     fx = _fx(effects)
-    S = _SceneF64(scene)
+    S, st0 = _scene_args(scene, cam)
     c = _cam(cam)
     n_all = int(c[16]) * int(c[17])
     px = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
@@ -219,7 +258,7 @@ def render(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int = 1 << 16,
                           _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d), R, _p(px, _i64),
                           float(eps), int(max_steps), tau, _p(rgb, _d), _p(tr, _d), _p(dp, _d),
                           _p(st, _i32), _p(ss, _u8), _p(fl, _u8), int(trace), _p(tc, _i32),
-                          _p(tt, _d), _p(fx, _d), int(threads))
+                          _p(tt, _d), _p(fx, _d), _p(st0, _d), int(threads))
     if rc:
         raise ValueError("oracle render: bad arguments")
     out = dict(rgb=rgb, trans=tr, depth=dp, steps=st, status=ss, flags=fl, tau=tau,
@@ -236,7 +275,7 @@ def render_quantile(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int =
     """Quantile loss of Eq. (6) per ray: E|W^-1(u1) - W^-1(u2)|, u1, u2 ~ U[0,1],
     W^-1 the quantile function of the ray's normalised weight distribution."""
     fx = _fx(effects)
-    S = _SceneF64(scene)
+    S, st0 = _scene_args(scene, cam)
     c = _cam(cam)
     n_all = int(c[16]) * int(c[17])
     px = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
@@ -245,7 +284,7 @@ def render_quantile(scene, cam, pixels=None, eps: float = 1e-4, max_steps: int =
     rc = lib().orc_render_quantile(S.n, _p(S.pos, _d), _p(S.off, _i64), _p(S.adj, _i32),
                                    _p(S.sigma, _d), _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d),
                                    R, _p(px, _i64), float(eps), int(max_steps), _p(q, _d),
-                                   _p(fx, _d), int(threads))
+                                   _p(fx, _d), _p(st0, _d), int(threads))
     if rc:
         raise ValueError("oracle render_quantile: bad arguments")
     return q
@@ -258,7 +297,7 @@ def render_bwd(scene, cam, g_rgb, g_trans=None, g_depth=None, pixels=None, eps: 
     + sum(g_quantile*quantile) with respect to density [N], SH [N,K,3] and
     positions [N,3]."""
     fx = _fx(effects)
-    S = _SceneF64(scene)
+    S, st0 = _scene_args(scene, cam)
     c = _cam(cam)
     n_all = int(c[16]) * int(c[17])
     px = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
@@ -275,7 +314,7 @@ def render_bwd(scene, cam, g_rgb, g_trans=None, g_depth=None, pixels=None, eps: 
                               _p(S.sigma, _d), _p(S.sh, _d), S.deg, _p(S.box, _d), _p(c, _d), R,
                               _p(px, _i64), float(eps), int(max_steps), _p(gr, _d), _p(gt, _d),
                               _p(gd, _d), _p(gq, _d), _p(g_sigma, _d), _p(g_sh, _d), _p(g_pos, _d),
-                              _p(fx, _d), int(threads))
+                              _p(fx, _d), _p(st0, _d), int(threads))
     if rc:
         raise ValueError("oracle render_bwd: bad arguments")
     return dict(density=g_sigma, sh=g_sh, pos=g_pos)

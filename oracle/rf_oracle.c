@@ -708,14 +708,31 @@ typedef struct {
     int degen;
 } cam_start_t;
 
-static cam_start_t camera_start(const scene_t *S, const double *cam, double tau)
+/* start_info, if given, holds {nn(centre), its gap} found by an earlier
+ * call of orc_camera_start for the same scene and camera. */
+static cam_start_t camera_start(const scene_t *S, const double *cam, double tau, const double *start_info)
 {
     const double o[3] = {cam[3], cam[7], cam[11]};  /* the centre (mid-frame for a rolling shutter) */
     double gap;
     cam_start_t c;
-    c.start = orc_nearest_site(S->n, S->pos, o, &gap);
+    if (start_info) {
+        c.start = (int64_t)start_info[0];
+        gap = start_info[1];
+    } else {
+        c.start = orc_nearest_site(S->n, S->pos, o, &gap);
+    }
     c.degen = gap < tau;
     return c;
+}
+
+/* nn of the camera centre and its gap (out2 = {site, gap}), for reuse by
+ * later calls on the same scene and camera. */
+void orc_camera_start(int64_t n_sites, const double *pos, const double *cam, double *out2)
+{
+    const double o[3] = {cam[3], cam[7], cam[11]};
+    double gap;
+    out2[0] = (double)orc_nearest_site(n_sites, pos, o, &gap);
+    out2[1] = gap;
 }
 
 static int64_t ray_start(const scene_t *S, const double *cam, const cam_start_t *c,
@@ -744,13 +761,13 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
                double eps, int max_steps, double tau,
                double *rgb, double *trans, double *depth, int32_t *steps, uint8_t *status,
                uint8_t *flags, int max_trace, int32_t *trace_cells, double *trace_t,
-               const double *effects, int n_threads)
+               const double *effects, const double *start_info, int n_threads)
 {
     scene_t S;
     if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
     effects_t E;
     const effects_t *EP = effects_of(effects, &E) ? &E : NULL;
-    const cam_start_t cs = camera_start(&S, cam, tau);
+    const cam_start_t cs = camera_start(&S, cam, tau, start_info);
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 64)
@@ -786,13 +803,14 @@ int orc_render(int64_t n_sites, const double *pos, const int64_t *off, const int
 int orc_render_quantile(int64_t n_sites, const double *pos, const int64_t *off, const int32_t *adj,
                         const double *sigma, const double *sh, int sh_degree, const double *box,
                         const double *cam, int64_t n_rays, const int64_t *pixels, double eps,
-                        int max_steps, double *quantile, const double *effects, int n_threads)
+                        int max_steps, double *quantile, const double *effects,
+                        const double *start_info, int n_threads)
 {
     scene_t S;
     if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
     effects_t E;
     const effects_t *EP = effects_of(effects, &E) ? &E : NULL;
-    const cam_start_t cs = camera_start(&S, cam, -1.0);
+    const cam_start_t cs = camera_start(&S, cam, -1.0, start_info);
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 64)
@@ -836,13 +854,13 @@ int orc_render_bwd(int64_t n_sites, const double *pos, const int64_t *off, const
                    double eps, int max_steps,
                    const double *g_rgb, const double *g_trans, const double *g_depth,
                    const double *g_quantile, double *g_sigma, double *g_sh, double *g_pos,
-                   const double *effects, int n_threads)
+                   const double *effects, const double *start_info, int n_threads)
 {
     scene_t S;
     if (setup_scene(&S, n_sites, pos, off, adj, sigma, sh, sh_degree, box)) return -1;
     effects_t E;
     const effects_t *EP = effects_of(effects, &E) ? &E : NULL;
-    const cam_start_t cs = camera_start(&S, cam, -1.0);
+    const cam_start_t cs = camera_start(&S, cam, -1.0, start_info);
     const int K = S.K;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);

@@ -344,3 +344,23 @@ def test_backward_matches_finite_differences(eye, fwd):
     untouched = np.setdiff1d(np.arange(sc.n_sites), visited)
     assert np.all(G["density"][untouched] == 0)
     assert np.all(G["sh"][untouched] == 0)
+
+
+def test_prepared_scene_gives_the_same_results():
+    # the FP64 copy and the start cell made once must not change any value
+    sc = random_scene(700, 2, 77)
+    cams = [camera_at((0.1, 0.2, -0.1), (1.0, 0.3, 0.2), w=11, h=9),
+            camera_at((2.2, -1.5, 0.7), (0.0, 0.0, 0.0), w=7, h=5)]
+    P = oracle.prepare(sc)
+    assert oracle.prepare(P) is P
+    for cam in cams:
+        a = oracle.render(sc, cam, trace=64)
+        b = oracle.render(P, cam, trace=64)
+        for k in ("rgb", "trans", "depth", "steps", "flags", "trace_cells"):
+            np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+        g = np.random.default_rng(1).normal(size=(cam.n_rays, 3))
+        ga = oracle.render_bwd(sc, cam, g)
+        gb = oracle.render_bwd(P, cam, g)
+        for k in ga:
+            np.testing.assert_allclose(ga[k], gb[k], rtol=1e-12, atol=1e-15)
+        assert P.start_info(cam)[0] == oracle.nearest_site(sc.pos, cam.c2w[:, 3])[0]
