@@ -5,8 +5,11 @@ One step = forward render + MSE loss gradient + backward (re-walk with
 gradient scatter) of one frame of the workload, all in the library's CUDA
 kernels, with the scene resident in HBM.  The headline value is forward +
 backward throughput in Mrays/s on the 3,000,000-site foam at 1920x1080
-(plain FP32 attributes); forward-only, BF16/FP16 attribute storage and
-serving latency are reported beside it.
+(plain FP32 attributes); forward-only, BF16/FP16 attribute storage, the
+4,096-site and 1M-site workloads, the 8-camera batch and serving latency are
+reported beside it.  The CPU-baseline leg (rank 0, one GPU) also compares the
+GPU with the FP64 oracle on sampled pixels: per-dtype image and gradient
+errors and the near-degenerate ray counts.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -16,6 +19,7 @@ all-reduce per step.  ``--impl reference`` times the FP64 CPU oracle on a
 bounded sample of the same workload.
 """
 import argparse
+import copy
 import json
 import math
 import os
@@ -75,23 +79,23 @@ def rank_camera(workload, rank):
 
 
 def bytes_per_step(k_bar, deg, attr_bytes):
-    """Algorithmic bytes one cell step reads (no reuse): cell header 16 B,
-    K faces x 12 B, the exit face's neighbour id 4 B, density and SH
-    coefficients."""
-    return 16 + 12 * k_bar + 4 + attr_bytes + 3 * (deg + 1) ** 2 * attr_bytes
-
-
-def replay_bytes_per_step(deg, attr_bytes):
-    """Algorithmic bytes one replayed backward step reads (no reuse): the
-    walk-record byte, cell header 16 B, the exit face 12 B, its neighbour id
-    4 B, density and SH coefficients."""
-    return 1 + 16 + 12 + 4 + attr_bytes + 3 * (deg + 1) ** 2 * attr_bytes
+    """Algorithmic bytes one forward cell step reads with no reuse: CSR
+    offsets 8 B, K faces x 16 B (a neighbour position and id), density and
+    the SH row (deg 3 FP32: 8 + 16 x 15.5 + 4 + 192 = 452 B)."""
+    return 8 + 16 * k_bar + attr_bytes + 3 * (deg + 1) ** 2 * attr_bytes
 
 
 def bwd_extra_bytes_per_step(deg):
-    """Backward: read-modify-write of the FP32 gradients touched per step:
-    density 4 B, SH 12 (deg+1)^2 B, and two site positions (one crossing) 24 B."""
+    """Backward: read-modify-write of the FP32 gradients one step touches:
+    density 4 B, SH 12 (deg+1)^2 B and two site positions (one crossing)
+    24 B (deg 3: 2 x 220 = 440 B)."""
     return 2 * (4 + 12 * (deg + 1) ** 2 + 24)
+
+
+# ncu counters of the renderer's kernels, per cell step, from the captures
+# summarised in profiles/ (valid only for the kernel sources they were taken on)
+COUNTERS = os.path.join(ROOT, "profiles", "kernel_counters.txt")
+L1_BYTES_PER_CLK = 128   # L1 load data path: one 128-byte wavefront per clock per SM
 
 
 def kernel_source_hash():
@@ -106,19 +110,46 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def measured_traffic(kernel, workload):
-    """DRAM bytes per launch of ``kernel`` on ``workload`` from the ncu
-    capture recorded in profiles/dram_traffic.txt, or None if that capture
-    was taken on other kernel sources."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    if not os.path.exists(path):
+def kernel_counters(kernel, workload):
+    """{dram, lts, l1_wavefronts}: bytes / wavefronts per cell step, and the
+    L1 LSU pipe and occupancy percentages, of ``kernel`` on ``workload`` from
+    profiles/kernel_counters.txt, or None when they were taken on other
+    kernel sources."""
+    if not os.path.exists(COUNTERS):
         return None
     src = kernel_source_hash()
-    for line in open(path):
+    for line in open(COUNTERS):
         f = line.split()
-        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == workload and f[2] == src:
-            return float(f[3])
+        if line.startswith("#") or len(f) < 9:
+            continue
+        if f[0] == kernel and f[1] == workload and f[2] == src:
+            steps = float(f[3])
+            return {"dram_bytes_per_step": float(f[4]) / steps, "lts_bytes_per_step": float(f[5]) / steps,
+                    "l1_wavefronts_per_step": float(f[6]) / steps, "l1_lsu_pct": float(f[7]),
+                    "occupancy_pct": float(f[8]), "source": src}
     return None
+
+
+def l2_copy_peak(dev, mb=48, reps=200):
+    """Device copy bandwidth within a buffer pair that stays in L2 (2 x 48 MB
+    of the 129 MB): read + write bytes over CUDA-event time, best of 3."""
+    import torch
+
+    a = torch.empty(mb << 18, device=dev)
+    b = torch.empty_like(a)
+    a.fill_(1.0)
+    for _ in range(10):
+        b.copy_(a)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
 
 
 # ---------------------------------------------------------------------------
@@ -175,7 +206,8 @@ class Clocks:
 # CPU oracle timing
 # ---------------------------------------------------------------------------
 def oracle_step(scene, cam, pixels, target):
-    import numpy as np
+    """One FP64 oracle training step on ``pixels``: forward, MSE gradient,
+    backward (``scene`` prepared once: FP64 arrays and nn(o) are not redone)."""
     import oracle
 
     o = oracle.render(scene, cam, pixels=pixels, tau=0.0)
@@ -191,10 +223,12 @@ def cpu_baseline(scene, cam, target, budget_s=12.0):
     R = cam.n_rays
     rng = np.random.default_rng(11)
     n = 2048
+    P = oracle.prepare(scene)
+    P.start_info(cam)
     while True:
         px = np.sort(rng.choice(R, size=min(n, R), replace=False)).astype(np.int64)
         t = time.perf_counter()
-        oracle_step(scene, cam, px, target)
+        oracle_step(P, cam, px, target)
         dt = time.perf_counter() - t
         if dt >= budget_s or n >= R or n >= (1 << 22):
             break
@@ -202,7 +236,8 @@ def cpu_baseline(scene, cam, target, budget_s=12.0):
     return {"value": len(px) / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"FP64 oracle fwd+bwd (MSE loss) on {len(px)} random pixels of the "
-                      f"{cam.width}x{cam.height} view, {dt:.1f} s"}
+                      f"{cam.width}x{cam.height} view, {dt:.1f} s (scene converted to FP64 and "
+                      f"nn(o) found once, outside the timing)"}
 
 
 def cpu_adjacency_baseline(pos, budget_s=6.0):
@@ -235,8 +270,9 @@ def run_reference(args):
     import oracle
     from paper_2502_01157_gb300 import scenes as S
 
-    scene = S.config_scene(args.workload, n_sites=args.sites or None)
+    scene = oracle.prepare(S.config_scene(args.workload, n_sites=args.sites or None))
     cam = rank_camera(args.workload, 0)
+    scene.start_info(cam)  # nn(o) once, like the FP64 conversion
     target = S.random_target(cam.n_rays, 2024)
     rng = np.random.default_rng(5)
     sample = 8192 if args.workload != "c1" else cam.n_rays
@@ -258,7 +294,8 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": f"{sample} random pixels per step of the "
-                                       f"{cam.width}x{cam.height} view, fwd+bwd"},
+                                       f"{cam.width}x{cam.height} view, fwd+bwd (scene converted to "
+                                       f"FP64 and nn(o) found once, before the steps)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -266,7 +303,9 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU
 # ---------------------------------------------------------------------------
-SERVE_RATES = (50, 200, 1000, 2000)
+SERVE_RATES = (50, 100, 200, 500, 1000, 2000)   # req/s: 2,000 requests or 10 s each
+SERVE_REQUESTS = 2000
+SERVE_SECONDS = 10.0
 
 
 def effects_extras(S, rf, foam, cam, target, scale, loss, grads, args, dev):
@@ -371,7 +410,7 @@ def mixture_extras(scene, args, dev):
     import torch
     from paper_2502_01157_gb300 import rf
     from paper_2502_01157_gb300 import scenes as S
-    from paper_2502_01157_gb300.serve import Server, run_open_loop
+    from paper_2502_01157_gb300.serve import Server, run_closed_loop, run_open_loop
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
     foam = rf.Foam.from_scene(scene)
@@ -409,14 +448,10 @@ def mixture_extras(scene, args, dev):
            "c4_rays": R,
            "c4_fwd_fp32_mrays_s": R * n / (a.elapsed_time(b) * 1e-3) / 1e6,
            "c4_fwdbwd_fp32_mrays_s": R * n / (b.elapsed_time(c) * 1e-3) / 1e6}
-    # serving poses and resolutions
+    # serving poses and resolutions; batched forward of 16 of them, FP32 vs BF16
     rng = np.random.default_rng(1005)
-    n_req = 4000
-    poses = S.sphere_poses(n_req, 12.0, 1005)
-    sizes = [S.C5_RESOLUTIONS[k] for k in rng.integers(0, 4, n_req)]
-    scams = [S.pinhole(w, h, 60.0, c2w=p) for (w, h), p in zip(sizes, poses)]
-    # batched forward of the first 64 serving requests, FP32 vs BF16 attributes
-    batch = scams[:16]
+    bposes = S.sphere_poses(16, 12.0, 1006)
+    batch = [S.pinhole(*S.C5_RESOLUTIONS[k], 60.0, c2w=p) for k, p in zip(rng.integers(0, 4, 16), bposes)]
     Rb = rf.n_rays_of(batch)
     for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
         foam.set_attributes(torch.from_numpy(scene.density).to(dev, dt),
@@ -430,23 +465,204 @@ def mixture_extras(scene, args, dev):
         b.record()
         torch.cuda.synchronize()
         res[f"serve_poses_batched_fwd_{name}_mrays_s"] = Rb * n / (a.elapsed_time(b) * 1e-3) / 1e6
-    # open-loop Poisson serving with BF16 attributes (set just above)
+    # open-loop Poisson serving with BF16 attributes (set just above): at each
+    # rate 2,000 requests or 10 s of arrivals, whichever is fewer
+    n_req = SERVE_REQUESTS
+    poses = S.sphere_poses(n_req, 12.0, 1005)
+    sizes = [S.C5_RESOLUTIONS[k] for k in rng.integers(0, 4, n_req)]
+    scams = [S.pinhole(w, h, 60.0, c2w=p) for (w, h), p in zip(sizes, poses)]
     srv = Server(foam, mem_budget_bytes=4 << 30, max_inflight=512, n_streams=4, max_batch=8)
     rates = []
     for k, rate in enumerate(SERVE_RATES):
-        m = int(min(n_req, max(100, rate * 2)))
+        m = int(min(SERVE_REQUESTS, rate * SERVE_SECONDS))
         arr = S.poisson_arrivals(float(rate), m, 500 + k)
         st = run_open_loop(srv, scams[:m], arr, deadline_s=60.0)
-        rates.append({"rate_req_s": rate, "offered": m, "completed": st["completed"],
-                      "rejected": st["rejected_open_loop"], "p50_ms": st["p50_ms"],
-                      "p99_ms": st["p99_ms"], "mrays_s": st["mrays_s"],
-                      "mean_batch": st["mean_batch"], "max_busy_streams": st["max_busy_streams"]})
+        offered_rays = sum(c.n_rays for c in scams[:m])
+        rates.append({"rate_req_s": rate, "offered": m, "offered_mrays_s": offered_rays / arr[-1] / 1e6,
+                      "completed": st["completed"], "rejected": st["rejected_open_loop"],
+                      "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                      "mrays_s": st["mrays_s"], "mean_batch": st["mean_batch"],
+                      "max_busy_streams": st["max_busy_streams"]})
+    # saturation: 64 requests kept in the server for 3 s
+    sat = run_closed_loop(srv, scams, 64, 3.0)
     srv.close()
     res["serving_bf16"] = {"budget_gb": 4, "streams": 4, "max_batch": 8,
                            "resolutions": "uniform over 320x240, 640x480, 1280x720, 1920x1080",
                            "poses": "uniform on the radius-12 sphere, looking at the origin",
-                           "rates": rates}
+                           "requests_per_rate": f"min({SERVE_REQUESTS}, {SERVE_SECONDS:.0f} s x rate)",
+                           "rates": rates,
+                           "saturation": {"inflight": 64, "seconds": 3.0, "completed": sat["completed"],
+                                          "mrays_s": sat["mrays_s"], "p50_ms": sat["p50_ms"],
+                                          "p99_ms": sat["p99_ms"], "mean_batch": sat["mean_batch"]}}
     foam.close()
+    return res
+
+
+def workload_extras(rf, scene, cam, args, dev, name):
+    """Throughput of another workload in the headline step's launch
+    configuration: forward alone and the training step (forward with a walk
+    record, MSE gradient, replayed backward), with cell steps and bytes."""
+    import torch
+
+    R = cam.n_rays
+    deg = scene.sh_degree
+    foam = rf.Foam.from_scene(scene)
+    target = torch.rand(R, 3, device=dev, generator=torch.Generator(dev).manual_seed(17))
+    grads = dict(density=torch.zeros(scene.n_sites, device=dev),
+                 sh=torch.zeros(scene.n_sites, (deg + 1) ** 2, 3, device=dev),
+                 pos=torch.zeros(scene.n_sites, 3, device=dev))
+    out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
+               depth=torch.empty(R, device=dev))
+    tout = dict(out, walk_record=(torch.empty(rf.walk_record_bytes([cam], RECORD_STEPS), dtype=torch.uint8,
+                                              device=dev), RECORD_STEPS))
+    steps_total = int(foam.render([cam], steps=True)["steps"].sum().item())
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step():
+        foam.render([cam], out=tout)
+        d, _ = rf.mse_grad(tout["rgb"], target, 1.0 / (3 * R))
+        foam.backward([cam], tout, d, grads=grads)
+
+    # a small frame is launch-bound: time enough iterations for ~0.2 s
+    n = max(args.steps, int(2e7 // max(R, 1)))
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    a, b, c = ev(), ev(), ev()
+    a.record()
+    for _ in range(n):
+        foam.render([cam], out=out)
+    b.record()
+    for _ in range(n):
+        step()
+    c.record()
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b) / n
+    step_ms = b.elapsed_time(c) / n
+    k_bar = scene.n_edges / scene.n_sites
+    fb = bytes_per_step(k_bar, deg, 4)
+    res = {"workload": f"{name}: {WORKLOADS[name]['desc']}", "rays": R, "n_sites": scene.n_sites,
+           "cell_steps_per_ray": steps_total / R, "iterations": n,
+           "fwd_ms": fwd_ms, "fwd_mrays_s": R / fwd_ms / 1e3, "fwd_cell_steps_per_s": steps_total / fwd_ms * 1e3,
+           "fwdbwd_ms": step_ms, "fwdbwd_mrays_s": R / step_ms / 1e3,
+           "fwdbwd_cell_steps_per_s": steps_total / step_ms * 1e3,
+           "fwd_algorithmic_gbs": fb * steps_total / fwd_ms / 1e6,
+           "fwdbwd_algorithmic_gbs": (2 * fb + bwd_extra_bytes_per_step(deg)) * steps_total / step_ms / 1e6,
+           "bytes_per_cell_step": {"fwd": fb, "fwd+bwd": 2 * fb + bwd_extra_bytes_per_step(deg)}}
+    foam.close()
+    return res
+
+
+def oracle_comparisons(rf, scene, cam, c1_scene, c2_scene, args, dev):
+    """The GPU against the FP64 oracle on sampled pixels (CPU-baseline leg):
+
+    * precision: for FP32 / BF16 / FP16 attribute storage, the image RMSE
+      against the oracle on the same rounded attributes (the compute error),
+      against the oracle on the FP32 originals (the storage error), and the
+      gradient's relative L2 error against the oracle's (loss on the sampled
+      rays without a near-degenerate flag, the forward's walk record replayed);
+    * the near-degenerate ray classes of the 4,096-site frame (all rays, with
+      the GPU's visited cells checked against the oracle's) and of the
+      sampled pixels of the other frames;
+    * the oracle's own forward (4,096 sites) and fwd+bwd (1M sites) timings on
+      the same rays as the GPU's."""
+    import numpy as np
+    import torch
+    import oracle
+
+    res = {}
+    rng = np.random.default_rng(31)
+    R = cam.n_rays
+    px = np.sort(rng.choice(R, size=1500, replace=False)).astype(np.int64)
+    pxt = torch.from_numpy(px).to(dev)
+    P32 = oracle.prepare(scene)
+    ref32 = oracle.render(P32, cam, pixels=px)
+    flags = {"c3_sample": oracle.flag_counts(ref32["flags"])}
+    keep = ~ref32["degen"]
+    w = rng.normal(size=(int(keep.sum()), 3))
+    prec = {}
+    torch_dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+    foam = rf.Foam.from_scene(scene)
+    for name, dt in torch_dt.items():
+        if name == "f32":
+            Pr, refr = P32, ref32
+        else:
+            sc_r = copy.copy(scene)
+            sc_r.density = torch.from_numpy(scene.density).to(dt).float().numpy()
+            sc_r.sh = torch.from_numpy(scene.sh).to(dt).float().numpy()
+            Pr = oracle.prepare(sc_r)
+            refr = oracle.render(Pr, cam, pixels=px)
+        foam.set_attributes(torch.from_numpy(scene.density).to(dev, dt), torch.from_numpy(scene.sh).to(dev, dt))
+        out = foam.render([cam], record=RECORD_STEPS)
+        g = {k: out[k][pxt].double().cpu().numpy() for k in ("rgb", "trans", "depth")}
+        rm = lambda a, b: float(np.sqrt(np.mean((a - b) ** 2)))
+        d_rgb = torch.zeros(R, 3, device=dev)
+        d_rgb[pxt[torch.from_numpy(keep).to(dev)]] = torch.from_numpy(w).float().to(dev)
+        G = foam.backward([cam], out, d_rgb)
+        Go = oracle.render_bwd(Pr, cam, w, pixels=px[keep])
+        rel = {k: float(np.linalg.norm(G[k].double().cpu().numpy() - Go[k]) / np.linalg.norm(Go[k]))
+               for k in ("density", "sh", "pos")}
+        prec[name] = {"compute_rmse": {k: rm(g[k], refr[k]) for k in g},
+                      "storage_rmse": {k: rm(g[k], ref32[k]) for k in g},
+                      "grad_rel_l2": rel}
+        del out, G
+        if Pr is not P32:
+            del Pr
+    foam.close()
+    res["precision"] = {"sample": f"{len(px)} random pixels of the {cam.width}x{cam.height} frame, "
+                                  f"{scene.n_sites} sites; gradients of a random linear loss on the "
+                                  f"{int(keep.sum())} unflagged ones, walk record replayed",
+                        "bounds": {"compute_rmse": 1e-5, "grad_rel_l2": 1e-3}, **prec}
+    # the 4,096-site frame: every ray, cells compared with the oracle's
+    if c1_scene is not None:
+        from paper_2502_01157_gb300 import scenes as S
+
+        cam1 = S.config_cameras("c1")[0]
+        f1 = rf.Foam.from_scene(c1_scene)
+        cells, counts = f1.trace(cam1, max_per_ray=256)
+        cells, counts = cells.cpu().numpy(), counts.cpu().numpy()
+        t = time.perf_counter()
+        o1 = oracle.render(c1_scene, cam1, trace=256)
+        bad = 0
+        for r in range(cam1.n_rays):
+            if o1["tie"][r]:
+                continue
+            n_o, n_g = int(o1["steps"][r]), int(counts[r])
+            if o1["stop_tie"][r] and abs(n_o - n_g) <= 1:
+                m = min(n_o, n_g, 256)
+            elif n_o == n_g:
+                m = min(n_o, 256)
+            else:
+                bad += 1
+                continue
+            bad += int(not np.array_equal(cells[r, :m], o1["trace_cells"][r, :m]))
+        flags["c1"] = dict(oracle.flag_counts(o1["flags"]), cells_mismatched_outside_ties=bad)
+        t = time.perf_counter()
+        oracle.render(c1_scene, cam1, tau=0.0)
+        dt = time.perf_counter() - t
+        res["c1_oracle"] = {"fwd_mrays_s": cam1.n_rays / dt / 1e6, "rays": cam1.n_rays,
+                            "cores": oracle.num_threads()}
+        f1.close()
+    if c2_scene is not None:
+        from paper_2502_01157_gb300 import scenes as S
+
+        cam2 = S.config_cameras("c2")[0]
+        P2 = oracle.prepare(c2_scene)
+        px2 = np.sort(rng.choice(cam2.n_rays, size=4096, replace=False)).astype(np.int64)
+        o2 = oracle.render(P2, cam2, pixels=px2[:1500])
+        flags["c2_sample"] = oracle.flag_counts(o2["flags"])
+        target = S.random_target(cam2.n_rays, 77)
+        t = time.perf_counter()
+        oracle_step(P2, cam2, px2, target)
+        dt = time.perf_counter() - t
+        res["c2_oracle"] = {"fwdbwd_mrays_s": len(px2) / dt / 1e6, "rays": int(len(px2)),
+                            "cores": oracle.num_threads()}
+        del P2
+    res["near_degenerate"] = {
+        "classes": "edge: passes within tau of a Voronoi edge or vertex (cells may differ); camera: "
+                   "start within tau of a bisector; stop: T within 1e-3 of eps at a stop test (may stop "
+                   "one step apart); graze / bend: gradient conditioning only (cells compared bit for bit)",
+        "tau": "1e-6 x max(1, |scene box|, |camera|)", **flags}
     return res
 
 
@@ -494,9 +710,11 @@ def main():
     scene = S.config_scene(args.workload, n_sites=args.sites or None)
     cam = rank_camera(args.workload, rank)
     target_np = S.random_target(cam.n_rays, 2024 + rank)
-    mix_scene = None
+    mix_scene = c1_scene = c2_scene = None
     if not args.no_extras and world == 1:
         mix_scene = S.config_scene("c4")  # 3M-site mixture: batched and serving workloads
+        c1_scene = S.config_scene("c1") if args.workload != "c1" else scene
+        c2_scene = S.config_scene("c2") if args.workload != "c2" else scene
 
     import torch
 
@@ -506,6 +724,7 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+    from paper_2502_01157_gb300 import dist as rfdist
     from paper_2502_01157_gb300 import rf
 
     R = cam.n_rays
@@ -538,8 +757,7 @@ def main():
         if marks is not None:
             marks[3].record()
         if world > 1:
-            for g in grads.values():
-                dist.all_reduce(g)
+            rfdist.allreduce_grads(grads)
 
     def barrier():
         if world > 1:
@@ -568,10 +786,7 @@ def main():
     ms = t0.elapsed_time(t1) / args.steps
     fwd_ms = sum(m[0].elapsed_time(m[1]) for m in marks) / args.steps
     bwd_ms = sum(m[2].elapsed_time(m[3]) for m in marks) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rfdist.max_over_ranks(ms, device=dev)
     value = world * R / (ms * 1e-3) / 1e6
 
     # forward-only throughput (rendering alone: no walk record)
@@ -635,6 +850,9 @@ def main():
         res["fwdbwd_quantile_fp32_mrays_s"] = R / (b.elapsed_time(c) / args.steps * 1e-3) / 1e6
         res["effects"] = effects_extras(S, rf, foam, cam, target, scale, loss, grads, args, dev)
         res["adjacency"] = adjacency_extras(rf, scene, mix_scene, args, dev)
+        for name, sc in (("c1", c1_scene), ("c2", c2_scene)):
+            if sc is not None and name != args.workload:
+                res[f"{name}_gpu"] = workload_extras(rf, sc, S.config_cameras(name)[0], args, dev, name)
 
     mixture = None
     if mix_scene is not None:
@@ -656,36 +874,56 @@ def main():
     e2e_s = (time.perf_counter() - w0) / args.steps
     barrier()
 
-    # roofline of the dominant kernel (the backward, replaying the walk record
-    # for the first RECORD_STEPS steps of every ray and searching after them)
+    # roofline of the dominant kernel.  The walk is a dependent gather whose
+    # neighbouring rays read the same cells, so its algorithmic bytes (what a
+    # cell step reads with no reuse) are served almost entirely by L1 and L2:
+    # the binding unit is the L1 load data path (ncu: the LSU pipe's
+    # wavefronts), whose ceiling is 128 bytes per clock per SM.  The DRAM and
+    # L2 blocks hold ncu's bytes per cell step over the live duration.
     attr_b = 4
-    fwd_bytes = (bytes_per_step(k_bar, deg, attr_b) + 1) * steps_total + 20 * R
-    steps_replayed = int(chk["steps"].clamp(max=RECORD_STEPS).sum().item())
-    bwd_step_bytes = (replay_bytes_per_step(deg, attr_b) * steps_replayed
-                      + bytes_per_step(k_bar, deg, attr_b) * (steps_total - steps_replayed)) / steps_total
-    bwd_bytes = (bwd_step_bytes + bwd_extra_bytes_per_step(deg)) * steps_total + 32 * R
-    import json as _j
-
+    fwd_step_b = bytes_per_step(k_bar, deg, attr_b)
+    bwd_step_b = fwd_step_b + bwd_extra_bytes_per_step(deg)
     peaks = {}
     try:
-        peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm, hbm_src = float(peaks["hbm_gbs"]), "measured"
     except Exception:
-        peak, peak_src = 6800.0, "fallback"
+        hbm, hbm_src = 6800.0, "fallback"
     dominant = "bwd" if bwd_ms >= fwd_ms else "fwd"
-    kb = bwd_bytes if dominant == "bwd" else fwd_bytes
     kms = bwd_ms if dominant == "bwd" else fwd_ms
-    achieved = kb / (kms * 1e-3) / 1e9
-    roof = {"kernel": f"rf::{dominant}_kernel<float,{deg}>", "bound": "hbm", "achieved": achieved,
-            "peak": peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic(f"{dominant}_kernel<float,{deg}>", args.workload if not args.sites else f"{args.workload}@{scene.n_sites}"),
-            "algorithmic_bytes_per_launch": kb, "kernel_source": kernel_source_hash(),
-            "note": "algorithmic bytes are served >99% by L1/L2 (traffic = ncu DRAM bytes per "
-                    "launch); the binding unit is the L1 load data path, see profiles/",
-            "bytes_per_cell_step": (bwd_step_bytes + bwd_extra_bytes_per_step(deg) if dominant == "bwd"
-                                    else bytes_per_step(k_bar, deg, attr_b) + 1),
-            "steps_replayed_frac": steps_replayed / steps_total,
-            "cell_steps_per_launch": steps_total, "ms_per_launch": kms}
+    step_b = bwd_step_b if dominant == "bwd" else fwd_step_b
+    kname = f"{dominant}_kernel<float,{deg}>"
+    wl = args.workload if not args.sites else f"{args.workload}@{scene.n_sites}"
+    achieved = step_b * steps_total / (kms * 1e-3) / 1e9
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = (clk or {}).get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    l1_peak = n_sm * L1_BYTES_PER_CLK * sm_mhz * 1e6 / 1e9
+    l2_peak = l2_copy_peak(dev)
+    cnt = kernel_counters(kname, wl)
+    roof = {"kernel": f"rf::{kname}", "bound": "l1", "unit": "GB/s",
+            "achieved": achieved, "peak": l1_peak, "frac": achieved / l1_peak,
+            "peak_source": f"derived: {n_sm} SMs x {L1_BYTES_PER_CLK} B/clock x {sm_mhz:.0f} MHz "
+                           "(median SM clock under load)",
+            "traffic": cnt["dram_bytes_per_step"] * steps_total if cnt else None,
+            "algorithmic_bytes_per_cell_step": step_b,
+            "algorithmic_bytes_per_launch": step_b * steps_total,
+            "cell_steps_per_launch": steps_total, "ms_per_launch": kms,
+            "reuse_vs_hbm": achieved / hbm,
+            "dram": ({"achieved": cnt["dram_bytes_per_step"] * steps_total / (kms * 1e-3) / 1e9,
+                      "peak": hbm, "peak_source": hbm_src, "unit": "GB/s"} if cnt else None),
+            "l2": ({"achieved": cnt["lts_bytes_per_step"] * steps_total / (kms * 1e-3) / 1e9,
+                    "peak": l2_peak, "peak_source": "measured: device copy within an L2-resident "
+                                                    "buffer pair, CUDA events", "unit": "GB/s"}
+                   if cnt else {"achieved": None, "peak": l2_peak}),
+            "l1_lsu_pct": cnt["l1_lsu_pct"] if cnt else None,
+            "occupancy_pct": cnt["occupancy_pct"] if cnt else None,
+            "counters_source": (f"profiles/kernel_counters.txt (kernel sources {cnt['source']})" if cnt
+                                else f"none for kernel sources {kernel_source_hash()}"),
+            "note": "bound = the L1 load data path (the LSU pipe's wavefronts, ncu); achieved = "
+                    "algorithmic bytes (no reuse) / live kernel time; reuse_vs_hbm = achieved / HBM copy peak"}
+    for blk in ("dram", "l2"):
+        if roof[blk] and roof[blk].get("achieved"):
+            roof[blk]["frac"] = roof[blk]["achieved"] / roof[blk]["peak"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -703,6 +941,7 @@ def main():
             **res,
             "mixture_3m": mixture,
             "gpu_launches": args.steps * 6,
+            "fwd_bytes_per_cell_step": fwd_step_b, "bwd_bytes_per_cell_step": bwd_step_b,
             "roofline": roof,
             "clocks": clk,
             "e2e": {"value": R / e2e_s / 1e6, "unit": UNIT,
@@ -712,6 +951,10 @@ def main():
         line["cpu_baseline"] = cpu_baseline(scene, cam, target_np)
         if not args.no_extras:
             line["cpu_baseline"]["adjacency"] = cpu_adjacency_baseline(scene.pos)
+            cmp_ = oracle_comparisons(rf, scene, cam, c1_scene, c2_scene, args, dev)
+            line["precision"] = cmp_.pop("precision")
+            line["near_degenerate"] = cmp_.pop("near_degenerate")
+            line["cpu_baseline"].update(cmp_)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

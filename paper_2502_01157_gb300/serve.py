@@ -116,3 +116,31 @@ def run_open_loop(server: Server, cams: List, arrivals: np.ndarray, poll_interva
     st["rejected_open_loop"] = rejected
     st["wall_s"] = time.perf_counter() - t0
     return st
+
+
+def run_closed_loop(server: Server, cams: List, inflight: int, duration_s: float,
+                    poll_interval_s: float = 1e-4) -> dict:
+    """Saturation load: keeps ``inflight`` requests in the server (a new one
+    is submitted as soon as one completes), cycling through ``cams``, for
+    ``duration_s``; returns the server's statistics (its Mrays/s is the
+    saturation throughput)."""
+    server.reset_stats()
+    pending = []
+    k = 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while now < duration_s and len(pending) < inflight:
+            rid = server.submit(cams[k % len(cams)])
+            if rid is None:
+                break
+            pending.append(rid)
+            k += 1
+        pending = [rid for rid in pending if not server.poll(rid)[0]]
+        if now >= duration_s and not pending:
+            break
+        time.sleep(poll_interval_s)
+    st = server.stats()
+    st["submitted"] = k
+    st["wall_s"] = time.perf_counter() - t0
+    return st

@@ -1,19 +1,34 @@
-"""The roofline accounting in bench.py: algorithmic bytes per cell step as
-stated for the forward (no reuse), the replayed backward and the gradient
-read-modify-write, and the clock-record parser."""
+"""The roofline accounting in bench.py: algorithmic bytes per cell step (what
+a step reads with no reuse: CSR offsets, one 16-byte record per face,
+density and the SH row; the backward adds the gradient read-modify-write),
+the counters file, the L1 ceiling, and the clock-record parser."""
 import bench
 
 
 def test_bytes_per_cell_step():
-    # header 16 + 15.5 faces x 12 + neighbour id 4 + density + SH
-    assert bench.bytes_per_step(15.5, 3, 4) == 16 + 186 + 4 + 4 + 192 == 402
-    assert bench.bytes_per_step(15.5, 3, 2) == 16 + 186 + 4 + 2 + 96 == 304
-    assert bench.bytes_per_step(15.5, 0, 4) == 16 + 186 + 4 + 4 + 12
-    # replayed backward: record byte, header, one exit face, its id, density, SH
-    assert bench.replay_bytes_per_step(3, 4) == 1 + 16 + 12 + 4 + 4 + 192 == 229
+    # offsets 8 + 15.5 faces x 16 + density + SH
+    assert bench.bytes_per_step(15.5, 3, 4) == 8 + 248 + 4 + 192 == 452
+    assert bench.bytes_per_step(15.5, 3, 2) == 8 + 248 + 2 + 96 == 354
+    assert bench.bytes_per_step(15.5, 0, 4) == 8 + 248 + 4 + 12 == 272
     # gradient read-modify-write: density, SH row, two site positions
     assert bench.bwd_extra_bytes_per_step(3) == 2 * (4 + 192 + 24) == 440
-    assert bench.replay_bytes_per_step(3, 4) + bench.bwd_extra_bytes_per_step(3) == 669
+    # fwd + bwd (re-walk) per step: 452 + 452 + 440
+    assert 2 * bench.bytes_per_step(15.5, 3, 4) + bench.bwd_extra_bytes_per_step(3) == 1344
+
+
+def test_kernel_counters_follow_the_sources(tmp_path, monkeypatch):
+    path = tmp_path / "kernel_counters.txt"
+    src = bench.kernel_source_hash()
+    path.write_text("# kernel workload sources steps dram lts l1_wavefronts lsu_pct occupancy\n"
+                    f"bwd_kernel<float,3> c3 {src} 1000 2000 30000 500000 76.5 35.5\n"
+                    "bwd_kernel<float,3> c3 0123456789ab 1000 9 9 9 9 9\n")
+    monkeypatch.setattr(bench, "COUNTERS", str(path))
+    c = bench.kernel_counters("bwd_kernel<float,3>", "c3")
+    assert c["dram_bytes_per_step"] == 2.0 and c["lts_bytes_per_step"] == 30.0
+    assert c["l1_wavefronts_per_step"] == 500.0 and c["l1_lsu_pct"] == 76.5
+    assert bench.kernel_counters("fwd_kernel<float,3>", "c3") is None
+    path.write_text(f"bwd_kernel<float,3> c3 0123456789ab 1000 9 9 9 9 9\n")
+    assert bench.kernel_counters("bwd_kernel<float,3>", "c3") is None   # other kernel sources
 
 
 def test_clock_record_parser(tmp_path, monkeypatch):

@@ -130,3 +130,30 @@ def test_fisheye_and_rolling_shutter_requests(foam):
         srv.wait(rid, out=img)
         np.testing.assert_array_equal(img, _image(foam, cam))
     srv.close()
+
+
+def test_served_images_match_the_oracle(foam):
+    """Requests of mixed sizes served concurrently: each image against the
+    FP64 oracle (on the BF16-rounded attributes the server renders) on
+    sampled pixels, within the image tolerance."""
+    import oracle
+    from tests.parity import IMG_RMSE
+
+    sc = random_scene(4000, 3, 77)
+    rng = np.random.default_rng(78)
+    sc.sh[:, 1:, :] = rng.normal(0, 0.3, sc.sh[:, 1:, :].shape).astype(np.float32)
+    sc.density = torch.from_numpy(sc.density).bfloat16().float().numpy()
+    sc.sh = torch.from_numpy(sc.sh).bfloat16().float().numpy()
+    P = oracle.prepare(sc)
+    cams = _cams(12, 5)
+    srv = Server(foam, mem_budget_bytes=64 << 20, max_inflight=64, n_streams=3, max_batch=4)
+    ids = [srv.submit(c) for c in cams]
+    assert all(r is not None for r in ids)
+    for rid, cam in zip(ids, cams):
+        img = np.zeros((cam.n_rays, 3), np.float32)
+        srv.wait(rid, out=img)
+        px = np.sort(rng.choice(cam.n_rays, size=min(256, cam.n_rays), replace=False))
+        o = oracle.render(P, cam, pixels=px)
+        err = float(np.sqrt(np.mean((img[px].astype(np.float64) - o["rgb"]) ** 2)))
+        assert err <= IMG_RMSE, f"{cam.width}x{cam.height}: rmse {err:.2e}"
+    srv.close()
