@@ -139,45 +139,21 @@ struct BwdIO {
     const float *qaux, *d_quantile;
 };
 
-template <int DEG>
-__device__ __forceinline__ void scatter_sh(float *__restrict__ g_sh, int i, const float *cb,
-                                           const float *Y, bool vec) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
-    constexpr int NV = 3 * K;
-    float *row = g_sh + (size_t)i * NV;
-    if constexpr (NV % 4 == 0) {
-        if (vec) {
-#pragma unroll
-            for (int q = 0; q < NV / 4; ++q) {
-                float4 v;
-                v.x = cb[(4 * q + 0) % 3] * Y[(4 * q + 0) / 3];
-                v.y = cb[(4 * q + 1) % 3] * Y[(4 * q + 1) / 3];
-                v.z = cb[(4 * q + 2) % 3] * Y[(4 * q + 2) / 3];
-                v.w = cb[(4 * q + 3) % 3] * Y[(4 * q + 3) / 3];
-                atomicAdd(reinterpret_cast<float4 *>(row) + q, v);
-            }
-            return;
-        }
-    }
-#pragma unroll
-    for (int g = 0; g < NV; ++g)
-        if (cb[g % 3] != 0.f) atomicAdd(row + g, cb[g % 3] * Y[g / 3]);
-}
-
 // Backward: the walk of the forward is repeated with identical arithmetic;
 // per segment the adjoints follow from the stored final colour, transmittance
 // and depth (C_rest = C_final - C_incl).
 //
 // Scatter.  Neighbouring rays of a warp mostly walk the same cells (a warp of
-// an 8x4 patch meets ~5 distinct cells per iteration at 1920x1080 and reuses
+// an 8x4 patch meets ~5-7 distinct cells per iteration at 1920x1080 and reuses
 // each ~25 times over its walk), so per-lane atomics would hit the same
-// addresses many times.  Each iteration the lanes stage their contributions
-// (SH row, density, the two site positions of the crossing that entered the
-// cell) in shared memory; lanes with the same (previous cell, cell) pair are
-// summed column-wise and the sums are added with 16-byte vector atomics: the
-// SH row into g_sh, the site terms into the {x, y, z, density} accumulator
-// g_acc that a final pass adds to g_pos and g_density.  A warp whose lanes
-// are spread over many cells scatters per lane.
+// addresses many times.  Each iteration the lanes stage their contributions to
+// the current cell (SH row, {position, density}) in shared memory; lanes in
+// the same cell are summed column-wise and the sums are added with 16-byte
+// vector atomics: the SH row into g_sh, the site terms into the
+// {x, y, z, density} accumulator g_acc that a final pass adds to g_pos and
+// g_density.  The rows of lanes alone in their cell are spread over the warp,
+// one 16-byte column per lane.  The crossing that entered the cell also moves
+// the previous cell's site; each lane adds those three terms to g_acc itself.
 constexpr int kMaxGroups = 12;
 
 template <typename AT, int DEG, bool QUANT, bool FX>
@@ -185,7 +161,7 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int NV = 3 * K;              // SH gradient row
     constexpr int NVP = (NV + 3) / 4 * 4;  // padded to whole 16-byte columns
-    constexpr int VP = NVP + 8;            // + {position of the cell, density}, {position of the previous cell, 0}
+    constexpr int VP = NVP + 4;            // + {position of the cell, density}
     // row stride: a multiple of 4 floats (16-byte row stores) whose quarter is
     // odd, so the 8 lanes of a 128-bit store phase hit 8 different bank quads;
     // a column read (one row, consecutive columns) is conflict-free for any stride
@@ -193,8 +169,13 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
     // one row per lane (+ a zero row that absent members read in the FX kernels)
     constexpr int ROWS = FX ? 33 : 32;
     __shared__ __align__(16) float stage_all[kBlock / 32][ROWS * SP];
+    // the lanes whose row is alone this iteration, and their cells, by rank
+    __shared__ int alone_lane_all[kBlock / 32][32];
+    __shared__ int alone_cell_all[kBlock / 32][32];
     const int lane = threadIdx.x & 31;
     float *stage = stage_all[threadIdx.x >> 5];
+    int *alone_lane = alone_lane_all[threadIdx.x >> 5];
+    int *alone_cell = alone_cell_all[threadIdx.x >> 5];
     const unsigned full = 0xffffffffu;
     if constexpr (FX) {
         for (int c = lane; c < SP; c += 32) stage[32 * SP + c] = 0.f;
@@ -398,26 +379,24 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
         }
 
         // ---- warp-wide scatter of this iteration's contributions ----
-        const unsigned long long key =
-            live ? (((unsigned long long)(uint32_t)key_prev << 32) | (uint32_t)i) : ~0ull;
-        const unsigned peers = __match_any_sync(full, key);
-        // lanes that share their (previous cell, cell) with another lane are
-        // summed through shared memory; a lane alone scatters by itself
-        const bool shared_row = live && __popc(peers) > 1;
-        const bool lead = shared_row && lane == __ffs(peers) - 1;
-        unsigned leaders = __ballot_sync(full, lead);
-        const bool grouped = __popc(leaders) <= kMaxGroups;
-        if (live && (!shared_row || !grouped)) {
-            if (io.g_sh && (cb[0] != 0.f || cb[1] != 0.f || cb[2] != 0.f)) scatter_sh<DEG>(io.g_sh, i, cb, Y, io.sh_vec);
-            if (sig_bar != 0.f || gpos_i[0] != 0.f || gpos_i[1] != 0.f || gpos_i[2] != 0.f)
-                atomicAdd(io.g_acc + i, make_float4(gpos_i[0], gpos_i[1], gpos_i[2], sig_bar));
-            if (key_prev >= 0 && (gpos_a[0] != 0.f || gpos_a[1] != 0.f || gpos_a[2] != 0.f))
-                atomicAdd(io.g_acc + key_prev, make_float4(gpos_a[0], gpos_a[1], gpos_a[2], 0.f));
-        }
-        if (grouped && leaders) {
-            if (shared_row) {
-                // this lane's row: SH gradient, density, position of the cell,
-                // position of the previous cell, zero padding
+        // The crossing that entered the cell also moves the previous cell's
+        // site: each lane adds those three terms itself.
+        if (live && key_prev >= 0 && (gpos_a[0] != 0.f || gpos_a[1] != 0.f || gpos_a[2] != 0.f))
+            atomicAdd(io.g_acc + key_prev, make_float4(gpos_a[0], gpos_a[1], gpos_a[2], 0.f));
+        // The rest goes to the current cell.  Lanes in the same cell are
+        // summed over 16-byte columns of their staged rows, two cells per
+        // pass; the rows of lanes alone in their cell (or of every lane, when
+        // the warp is spread over more than kMaxGroups shared cells) are
+        // spread over the whole warp, one (row, column) item per lane.
+        const unsigned peers = __match_any_sync(full, live ? (unsigned)i : 0xffffffffu);
+        const bool in_group = live && __popc(peers) > 1;
+        unsigned leaders = __ballot_sync(full, in_group && lane == __ffs(peers) - 1);
+        if (__popc(leaders) > kMaxGroups) leaders = 0u;
+        const bool alone = live && !(in_group && leaders != 0u);
+        const unsigned lone = __ballot_sync(full, alone);
+        if (leaders | lone) {
+            if (live) {
+                // this lane's row: SH gradient (zero padded), {position of the cell, density}
                 float4 *row = reinterpret_cast<float4 *>(stage + lane * SP);
 #pragma unroll
                 for (int q4 = 0; q4 < VP / 4; ++q4) {
@@ -427,20 +406,37 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                         const int c = 4 * q4 + e;
                         v[e] = c < NV ? cb[c % 3] * Y[c / 3]
                              : c < NVP ? 0.f
-                             : c < NVP + 3 ? gpos_i[c - NVP]
-                             : c == NVP + 3 ? sig_bar
-                             : c < NVP + 7 ? gpos_a[c - NVP - 4] : 0.f;
+                             : c < NVP + 3 ? gpos_i[c - NVP] : sig_bar;
                     }
                     row[q4] = make_float4(v[0], v[1], v[2], v[3]);
                 }
             }
+            if (alone) {
+                const int rank = __popc(lone & ((1u << lane) - 1u));
+                alone_lane[rank] = lane;
+                alone_cell[rank] = i;
+            }
             __syncwarp();
-            // 16-byte columns: lanes 0..15 sum the first group of a pass,
-            // lanes 16..31 the second; a lane sums four values at once and
-            // adds them with one vector atomic where they are four SH values
             constexpr int NQ = VP / 4;
             constexpr int SQ = SP / 4;
             const float4 *stage4 = reinterpret_cast<const float4 *>(stage);
+            // column c (floats 4c .. 4c+3) of a row of `cell` into the gradients
+            auto add_column = [&](int cell, int col, const float4 &v) {
+                const int c = 4 * col;
+                if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) return;
+                if (c >= NVP) {
+                    atomicAdd(io.g_acc + cell, v);   // {position, density} of the cell
+                } else if (NV % 4 == 0 && io.sh_vec) {
+                    atomicAdd(reinterpret_cast<float4 *>(io.g_sh + (size_t)cell * NV + c), v);
+                } else {
+                    const float v4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (c + j < NV && v4[j] != 0.f) atomicAdd(io.g_sh + (size_t)cell * NV + c + j, v4[j]);
+                }
+            };
+            // (a) cells shared by several lanes: lanes 0..15 sum the first
+            // cell of a pass, lanes 16..31 the second, four values per lane
             const int hl = lane & 15;
             while (leaders) {
                 const int L0 = __ffs(leaders) - 1;
@@ -451,9 +447,8 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                 const int L = lane >= 16 ? L1 : L0;
                 const unsigned m = __shfl_sync(full, peers, L);
                 const int cell_i = __shfl_sync(full, i, L);
-                const int cell_a = __shfl_sync(full, key_prev, L);
                 if ((lane < 16 || two) && hl < NQ) {
-                    // four members per pass with independent loads; an absent
+                    // four members per trip with independent loads; an absent
                     // member (-1) loads nothing
                     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
                     float4 sm = z4;
@@ -482,22 +477,14 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                         sm.z += (a0.z + a1.z) + (a2.z + a3.z);
                         sm.w += (a0.w + a1.w) + (a2.w + a3.w);
                     }
-                    const int c = 4 * hl;
-                    const bool nz = sm.x != 0.f || sm.y != 0.f || sm.z != 0.f || sm.w != 0.f;
-                    if (!nz) {
-                    } else if (c >= NVP) {
-                        // {position, density} of the cell, {position, 0} of the previous cell
-                        if (c == NVP) atomicAdd(io.g_acc + cell_i, sm);
-                        else if (cell_a >= 0) atomicAdd(io.g_acc + cell_a, sm);
-                    } else if (NV % 4 == 0 && io.sh_vec) {
-                        atomicAdd(reinterpret_cast<float4 *>(io.g_sh + (size_t)cell_i * NV + c), sm);
-                    } else {
-                        const float v4[4] = {sm.x, sm.y, sm.z, sm.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (c + j < NV && v4[j] != 0.f) atomicAdd(io.g_sh + (size_t)cell_i * NV + c + j, v4[j]);
-                    }
+                    add_column(cell_i, hl, sm);
                 }
+            }
+            // (b) rows alone: item t = (row rank t / NQ, column t % NQ)
+            const int items = __popc(lone) * NQ;
+            for (int t = lane; t < items; t += 32) {
+                const int r = t / NQ, col = t - r * NQ;
+                add_column(alone_cell[r], col, stage4[alone_lane[r] * SQ + col]);
             }
             __syncwarp();
         }
