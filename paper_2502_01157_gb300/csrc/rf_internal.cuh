@@ -359,12 +359,9 @@ constexpr int kRecNoExit = 0xFF;  // the cell had no exit
 
 __device__ __forceinline__ int exit_of_slot(const SceneDev &s, const CellHdr &c, const float3 &d,
                                             const float3 &oc, int slot, float &nb, float &db) {
-    const float4 *f = s.faces + 3 * ((size_t)c.gbeg + (slot >> 2));
-    const float4 X = ldg(f), Y = ldg(f + 1), Z = ldg(f + 2);
-    const int e = slot & 3;
-    const float x = e == 0 ? X.x : e == 1 ? X.y : e == 2 ? X.z : X.w;
-    const float y = e == 0 ? Y.x : e == 1 ? Y.y : e == 2 ? Y.z : Y.w;
-    const float z = e == 0 ? Z.x : e == 1 ? Z.y : e == 2 ? Z.z : Z.w;
+    // only the recorded face's three components: 12 bytes, not the group's 48
+    const float *f = reinterpret_cast<const float *>(s.faces + 3 * ((size_t)c.gbeg + (slot >> 2))) + (slot & 3);
+    const float x = ldg(f), y = ldg(f + 4), z = ldg(f + 8);
     db = __fmaf_rn(x, d.x, __fmaf_rn(y, d.y, __fmul_rn(z, d.z)));
     nb = __fmaf_rn(-x, oc.x, __fmaf_rn(-y, oc.y, __fmaf_rn(-z, oc.z, 1.f)));
     return ldg(s.nbr + 4 * (size_t)c.gbeg + slot);
