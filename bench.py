@@ -736,8 +736,8 @@ def main():
     grads = dict(density=torch.zeros(scene.n_sites, device=dev),
                  sh=torch.zeros(scene.n_sites, (deg + 1) ** 2, 3, device=dev),
                  pos=torch.zeros(scene.n_sites, 3, device=dev))
-    # the forward keeps a walk record (which face each step left by) that the
-    # backward replays instead of searching the faces again
+    # the forward keeps a segment record (exit, t1, density, colour per step)
+    # that the backward rebuilds its walk from
     out = dict(rgb=torch.empty(R, 3, device=dev), trans=torch.empty(R, device=dev),
                depth=torch.empty(R, device=dev),
                walk_record=(torch.empty(rf.walk_record_bytes([cam], RECORD_STEPS), dtype=torch.uint8,

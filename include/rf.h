@@ -240,16 +240,22 @@ RF_API rf_status rf_render_bwd(rf_scene *scene, const rf_camera *cams, int32_t n
  *     quantile           optional float [R]
  *     quantile_aux       float [R][5], required with quantile: per-ray sums the
  *                        backward of the quantile loss reads
- *     walk_record        optional device buffer of walk_record_bytes >=
+ *     walk_record        optional device buffer, 16-byte aligned, of
+ *                        walk_record_bytes >=
  *                        rf_walk_record_bytes(cams, n_cams, walk_record_steps):
  *                        the forward stores there, for the first
- *                        walk_record_steps steps of every ray, which face it
- *                        left each cell by (one byte per step).  Given to
- *                        rf_render_bwd_ex with the same cameras, options and
- *                        scene, it lets the backward replay those steps
- *                        instead of searching the faces again; the gradients
- *                        are the same up to the order of the floating-point
- *                        atomics.
+ *                        walk_record_steps steps of every ray, the segment it
+ *                        composited (Eq. 3-4): the neighbour it left the cell
+ *                        for, the exit parameter, the cell's density and its
+ *                        colour before the clamp (24 bytes per step).  Given
+ *                        to rf_render_bwd_ex with the same cameras, options
+ *                        and scene, it lets the backward rebuild those steps
+ *                        instead of reading the faces and attributes again;
+ *                        the gradients are the same up to the order of the
+ *                        floating-point atomics.  A record of another scene
+ *                        gives wrong gradients; a neighbour id outside the
+ *                        scene ends that ray's backward walk (no access out of
+ *                        bounds).
  */
 typedef struct rf_fwd_outputs {
     float *rgb;
@@ -291,8 +297,9 @@ typedef struct rf_bwd_inputs {
     int32_t walk_record_steps;
 } rf_bwd_inputs;
 
-/* Bytes of a walk record of `steps` steps per ray for these cameras (the
- * rays are grouped by warps of 32 on 16x8 tiles); 0 for bad arguments. */
+/* Bytes of a walk record of `steps` steps per ray for these cameras: 24
+ * bytes per step for every ray slot of the 16x8 tiles (rays are grouped by
+ * warps of 32); 0 for bad arguments. */
 RF_API size_t rf_walk_record_bytes(const rf_camera *cams, int32_t n_cams, int32_t steps);
 
 typedef struct rf_grads {

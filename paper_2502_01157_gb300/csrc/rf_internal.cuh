@@ -47,6 +47,7 @@ struct SceneDev {
     float box_hi[3];
     int32_t count_bits;  // low bits of a header's w that hold its group count
     int32_t sh_v8;       // SH rows are 32-byte aligned (base and row size)
+    int32_t n_sites;
 };
 
 // Cameras of one launch and the tile partition of their images.
@@ -73,7 +74,7 @@ struct RenderParams {
     float eps;
     int32_t max_steps;
     SphereFx fx;
-    uint8_t *rec;                          // walk record of this launch (warp-major) or null
+    uint32_t *rec;                         // segment record of this launch (warp-major) or null
     int32_t rec_steps;                     // recorded steps per ray
 };
 
@@ -351,22 +352,6 @@ __device__ __forceinline__ int find_exit(const SceneDev &s, const CellHdr &c, co
     return fb >= 0 ? ldg(s.nbr + 4 * (size_t)c.gbeg + fb) : -1;
 }
 
-// Walk record: the forward stores, per ray step, the slot of the exit face it
-// found (one byte); the backward replays that face instead of testing them
-// all, with the same arithmetic as face_test, so it gets the same exit.
-constexpr int kRecSearch = 0xFE;  // not recorded (slot too large): search again
-constexpr int kRecNoExit = 0xFF;  // the cell had no exit
-
-__device__ __forceinline__ int exit_of_slot(const SceneDev &s, const CellHdr &c, const float3 &d,
-                                            const float3 &oc, int slot, float &nb, float &db) {
-    // only the recorded face's three components: 12 bytes, not the group's 48
-    const float *f = reinterpret_cast<const float *>(s.faces + 3 * ((size_t)c.gbeg + (slot >> 2))) + (slot & 3);
-    const float x = ldg(f), y = ldg(f + 4), z = ldg(f + 8);
-    db = __fmaf_rn(x, d.x, __fmaf_rn(y, d.y, __fmul_rn(z, d.z)));
-    nb = __fmaf_rn(-x, oc.x, __fmaf_rn(-y, oc.y, __fmaf_rn(-z, oc.z, 1.f)));
-    return ldg(s.nbr + 4 * (size_t)c.gbeg + slot);
-}
-
 // One segment's bounds, width, density and colour (shared by all kernels).
 struct Segment {
     float t1;      // raw exit parameter (inf: no exit)
@@ -379,28 +364,11 @@ struct Segment {
     bool hit;      // the segment ends on the sphere at ts (FX kernels)
 };
 
-// With FX, ts is the current ray's next sphere crossing (+inf: none): when it
-// falls in [t0, t1) and before t_max the segment ends there instead of at the
-// face.
-// replay >= 0: the walk record's code for this step (the exit slot, or
-// kRecNoExit); otherwise the faces are searched and *code (if given) receives
-// the record code of the exit found.
-template <typename AT, int DEG, bool FX = false>
-__device__ __forceinline__ void cell_step(const SceneDev &s, int i, const CellHdr &cell,
-                                          const float3 &o, const float3 &d, float t0, float tmin,
-                                          float tmax, const float *Y, Segment &g, float3 &oc,
-                                          float ts = 0.f, int replay = -1, int *code = nullptr) {
-    oc = make_float3(__fsub_rn(o.x, cell.x), __fsub_rn(o.y, cell.y), __fsub_rn(o.z, cell.z));
-    float nb = 1.f, db = 0.f;
-    // a slot beyond the cell's faces (a record of another scene) is searched
-    if (replay >= 0 && replay != kRecSearch && (replay == kRecNoExit || replay < 4 * cell.gcnt)) {
-        g.next = replay == kRecNoExit ? -1 : exit_of_slot(s, cell, d, oc, replay, nb, db);
-    } else {
-        int slot;
-        g.next = find_exit(s, cell, d, oc, nb, db, slot);
-        if (code) *code = g.next < 0 ? kRecNoExit : slot < kRecSearch ? slot : kRecSearch;
-    }
-    g.t1 = g.next >= 0 ? __fdiv_rn(nb, db) : __int_as_float(0x7f800000);
+// Composited part [a, b) of the segment [t0, t1) clipped to [t_min, t_max)
+// and, with FX, ended early by a sphere crossing at ts in [t0, t1) before
+// t_max; its width delta = max(b - a, 0) and transmittance factor e.
+template <bool FX>
+__device__ __forceinline__ void segment_bounds(Segment &g, float t0, float tmin, float tmax, float ts) {
     g.a = t0 > tmin ? t0 : tmin;
     float tend = g.t1;
     g.hit = false;
@@ -411,9 +379,72 @@ __device__ __forceinline__ void cell_step(const SceneDev &s, int i, const CellHd
     g.b = tend < tmax ? tend : tmax;
     const float w = __fsub_rn(g.b, g.a);
     g.delta = w > 0.f ? w : 0.f;
-    g.sigma = to_f(ldg(reinterpret_cast<const AT *>(s.density) + i));
     g.e = expf(-__fmul_rn(g.sigma, g.delta));
+}
+
+// With FX, ts is the current ray's next sphere crossing (+inf: none): when it
+// falls in [t0, t1) and before t_max the segment ends there instead of at the
+// face.
+template <typename AT, int DEG, bool FX = false>
+__device__ __forceinline__ void cell_step(const SceneDev &s, int i, const CellHdr &cell,
+                                          const float3 &o, const float3 &d, float t0, float tmin,
+                                          float tmax, const float *Y, Segment &g, float3 &oc,
+                                          float ts = 0.f) {
+    oc = make_float3(__fsub_rn(o.x, cell.x), __fsub_rn(o.y, cell.y), __fsub_rn(o.z, cell.z));
+    float nb = 1.f, db = 0.f;
+    int slot;
+    g.next = find_exit(s, cell, d, oc, nb, db, slot);
+    g.t1 = g.next >= 0 ? __fdiv_rn(nb, db) : __int_as_float(0x7f800000);
+    g.sigma = to_f(ldg(reinterpret_cast<const AT *>(s.density) + i));
+    segment_bounds<FX>(g, t0, tmin, tmax, ts);
     sh_colour<AT, DEG>(reinterpret_cast<const AT *>(s.sh), i, Y, g.pre, s.sh_v8 != 0);
+}
+
+// Segment record.  In a training step the forward keeps, for each of the
+// first rec_steps steps of a ray, what the backward needs of the segment:
+// the exit neighbour, the raw exit parameter t1, the density and the colour
+// before the clamp (24 bytes).  Warp-major: per warp and step one row of six
+// 32-lane columns, so a warp stores and loads each field as one coalesced
+// 128-byte line, with streaming cache hints (the record is read once, by the
+// backward, and must not evict the scene from L2).  The backward rebuilds the
+// segment from it with the arithmetic of cell_step (segment_bounds), so it
+// meets the same bits without reading the faces or the attributes again.
+constexpr int kRecWords = 6;
+
+// This lane's column of its warp's record (null without a record).
+__device__ __forceinline__ uint32_t *record_column(const RenderParams &p) {
+    if (!p.rec) return nullptr;
+    return p.rec + ((int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5)) * p.rec_steps * (32 * kRecWords) +
+           (threadIdx.x & 31);
+}
+
+__device__ __forceinline__ void record_store(uint32_t *col, int k, const Segment &g) {
+    uint32_t *r = col + (int64_t)k * (32 * kRecWords);
+    __stcs(reinterpret_cast<int *>(r), g.next);
+    __stcs(reinterpret_cast<float *>(r + 32), g.t1);
+    __stcs(reinterpret_cast<float *>(r + 64), g.sigma);
+    __stcs(reinterpret_cast<float *>(r + 96), g.pre[0]);
+    __stcs(reinterpret_cast<float *>(r + 128), g.pre[1]);
+    __stcs(reinterpret_cast<float *>(r + 160), g.pre[2]);
+}
+
+// The recorded segment of step k in the current cell (position `cell`).  An
+// exit id outside the scene (a record of another scene) ends the walk there.
+template <bool FX>
+__device__ __forceinline__ void record_step(const SceneDev &s, const uint32_t *col, int k, const CellHdr &cell,
+                                            const float3 &o, float t0, float tmin, float tmax, Segment &g,
+                                            float3 &oc, float ts = 0.f) {
+    const uint32_t *r = col + (int64_t)k * (32 * kRecWords);
+    oc = make_float3(__fsub_rn(o.x, cell.x), __fsub_rn(o.y, cell.y), __fsub_rn(o.z, cell.z));
+    const int next = __ldcs(reinterpret_cast<const int *>(r));
+    g.t1 = __ldcs(reinterpret_cast<const float *>(r + 32));
+    g.sigma = __ldcs(reinterpret_cast<const float *>(r + 64));
+    g.pre[0] = __ldcs(reinterpret_cast<const float *>(r + 96));
+    g.pre[1] = __ldcs(reinterpret_cast<const float *>(r + 128));
+    g.pre[2] = __ldcs(reinterpret_cast<const float *>(r + 160));
+    g.next = next >= 0 && next < s.n_sites ? next : -1;
+    if (g.next < 0) g.t1 = __int_as_float(0x7f800000);
+    segment_bounds<FX>(g, t0, tmin, tmax, ts);
 }
 
 // ---------------------------------------------------------------------------

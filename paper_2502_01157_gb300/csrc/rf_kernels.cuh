@@ -59,11 +59,8 @@ __global__ void __launch_bounds__(kBlock, FX ? 6 : 8) fwd_kernel(const RenderPar
         float t0 = 0.f;
         FxRay f;
         if constexpr (FX) fx_begin(p.fx, o, d, f);
-        // this lane's column of its warp's walk record
-        uint8_t *rec = (!TRACE && p.rec)
-                           ? p.rec + ((int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5)) * p.rec_steps * 32 +
-                                 (threadIdx.x & 31)
-                           : nullptr;
+        // this lane's column of its warp's segment record
+        uint32_t *rec = TRACE ? nullptr : record_column(p);
         while (T > p.eps) {
             if (steps >= p.max_steps) {
                 st = RF_RAY_MAX_STEPS;
@@ -72,9 +69,8 @@ __global__ void __launch_bounds__(kBlock, FX ? 6 : 8) fwd_kernel(const RenderPar
             const CellHdr cell = load_cell(p.s, i);
             Segment g;
             float3 oc;
-            int code = kRecSearch;
-            cell_step<AT, DEG, FX>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc, FX ? f.ts : 0.f, -1, &code);
-            if (rec && steps < p.rec_steps) rec[32 * steps] = (uint8_t)code;
+            cell_step<AT, DEG, FX>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc, FX ? f.ts : 0.f);
+            if (rec && steps < p.rec_steps) record_store(rec, steps, g);
             if (TRACE && steps < out.max_trace) out.trace[r * out.max_trace + steps] = i;
             const float alpha = __fsub_rn(1.f, g.e);
             const float w = __fmul_rn(T, alpha);
@@ -233,11 +229,8 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
     int i = live ? start_cell<FX>(p, px.cam, o) : 0;
     FxRay f;
     if constexpr (FX) fx_begin(p.fx, o, d, f);
-    // the forward's walk record of this warp (lane column), if given: step k
-    // of a live lane is iteration k of the warp
-    const uint8_t *rec = p.rec ? p.rec + ((int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5)) * p.rec_steps * 32 +
-                                     (threadIdx.x & 31)
-                               : nullptr;
+    // the forward's segment record of this warp (lane column), if given
+    const uint32_t *rec = record_column(p);
     float t0 = 0.f, T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     int steps = 0;
     // the crossing that entered the current cell: (pa -> i) at pt; its adjoint
@@ -277,8 +270,10 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
         float3 oc = make_float3(0.f, 0.f, 0.f);
         if (live) {
             cell = load_cell(p.s, i);
-            const int replay = rec && steps < p.rec_steps ? (int)rec[32 * steps] : -1;
-            cell_step<AT, DEG, FX>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc, FX ? f.ts : 0.f, replay);
+            if (rec && steps < p.rec_steps)
+                record_step<FX>(p.s, rec, steps, cell, o, t0, tmin, tmax, g, oc, FX ? f.ts : 0.f);
+            else
+                cell_step<AT, DEG, FX>(p.s, i, cell, o, d, t0, tmin, tmax, Y, g, oc, FX ? f.ts : 0.f);
             const float alpha = __fsub_rn(1.f, g.e);
             const float w = __fmul_rn(T, alpha);
             const float c[3] = {fmaxf(g.pre[0], 0.f), fmaxf(g.pre[1], 0.f), fmaxf(g.pre[2], 0.f)};

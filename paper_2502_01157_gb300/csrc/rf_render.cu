@@ -66,17 +66,19 @@ __global__ void add_site_grads_kernel(const float4 *__restrict__ acc, int64_t n,
 // Host side
 // ---------------------------------------------------------------------------
 
-// Walk-record bytes of the launch holding cams[first .. first + count).
+// Segment-record bytes of the launch holding cams[first .. first + count):
+// per warp of a tile and recorded step, 32 lanes x kRecWords 4-byte words.
 static size_t record_bytes_of(const rf_camera *cams, int first, int count, int32_t steps) {
     int64_t tiles = 0;
     for (int c = first; c < first + count; ++c)
         tiles += (int64_t)((cams[c].width + kTileW - 1) / kTileW) * ((cams[c].height + kTileH - 1) / kTileH);
-    return (size_t)tiles * (kBlock / 32) * (size_t)steps * 32;
+    return (size_t)tiles * (kBlock / 32) * (size_t)steps * 32 * kRecWords * sizeof(uint32_t);
 }
 
 static rf_status check_record(const rf_camera *cams, int32_t n_cams, const void *rec, size_t bytes, int32_t steps) {
     if (!rec) return RF_OK;
     if (steps < 1 || steps > (1 << 20)) return fail(RF_ERR_INVALID_ARG, "walk_record_steps must be in [1, 2^20]");
+    if ((uintptr_t)rec & 15) return fail(RF_ERR_INVALID_ARG, "walk_record must be 16-byte aligned");
     size_t need = 0;
     for (int first = 0; first < n_cams; first += kMaxCamsPerLaunch)
         need += record_bytes_of(cams, first, std::min(n_cams - first, kMaxCamsPerLaunch), steps);
@@ -152,7 +154,7 @@ static rf_status render_fwd_impl(rf_scene *s, const rf_camera *cams, int32_t n_c
         const int64_t tiles = make_launch_cams(cams, first, count, ray_begin, &p.lc);
         if (tiles >= (1ll << 31)) return fail(RF_ERR_INVALID_ARG, "too many tiles in one launch");
         for (int c = 0; c < count; ++c) ray_begin += (int64_t)cams[first + c].width * cams[first + c].height;
-        p.rec = rec ? rec + rec_off : nullptr;
+        p.rec = rec ? reinterpret_cast<uint32_t *>(rec + rec_off) : nullptr;
         if (rec) rec_off += record_bytes_of(cams, first, count, rec_steps);
         launch_fwd_fx(p, s->attr_dtype, s->sh_degree, mode, tiles, out, st);
         RF_CUDA(cudaGetLastError());
@@ -239,7 +241,8 @@ RF_API rf_status rf_render_bwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_
         const int64_t tiles = make_launch_cams(cams, first, count, ray_begin, &p.lc);
         if (tiles >= (1ll << 31)) return fail(RF_ERR_INVALID_ARG, "too many tiles in one launch");
         for (int c = 0; c < count; ++c) ray_begin += (int64_t)cams[first + c].width * cams[first + c].height;
-        p.rec = in->walk_record ? const_cast<uint8_t *>(in->walk_record) + rec_off : nullptr;
+        p.rec = in->walk_record ? reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(in->walk_record) + rec_off)
+                                : nullptr;
         if (in->walk_record) rec_off += record_bytes_of(cams, first, count, in->walk_record_steps);
         launch_bwd_fx(p, s->attr_dtype, s->sh_degree, quant, tiles, io, st);
         RF_CUDA(cudaGetLastError());

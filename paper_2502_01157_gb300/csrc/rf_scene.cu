@@ -48,6 +48,7 @@ SceneDev scene_dev(const rf_scene *s) {
     d.nbr = s->nbr;
     d.count_bits = s->count_bits;
     d.sh_v8 = s->sh_v8;
+    d.n_sites = (int32_t)s->n_sites;
     d.density = s->density;
     d.sh = s->sh;
     for (int a = 0; a < 3; ++a) {

@@ -81,12 +81,13 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
 
 def test_walk_record_bytes_without_gpu(L):
     """Host-side sizing of the walk record: 4 warps of 32 rays per 16x8 tile,
-    one byte per step, launches of up to 16 cameras concatenated."""
+    24 bytes per step (exit id, t1, density, three colour values), launches
+    of up to 16 cameras concatenated."""
     from paper_2502_01157_gb300 import scenes as S
     cams = [S.pinhole(w, h, 60.0) for w, h in [(1920, 1080), (17, 9), (1, 1)] * 7]   # 21 cameras
     tiles = sum(((c.width + 15) // 16) * ((c.height + 7) // 8) for c in cams)
     for steps in (1, 7, 384):
-        assert rf.walk_record_bytes(cams, steps) == tiles * 4 * steps * 32
+        assert rf.walk_record_bytes(cams, steps) == tiles * 4 * steps * 32 * 24
     ca = rf.camera_array(cams)
     assert L.rf_walk_record_bytes(ca, len(ca), 0) == 0
     assert L.rf_walk_record_bytes(None, 3, 8) == 0

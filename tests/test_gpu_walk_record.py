@@ -1,6 +1,7 @@
-"""Walk record: the forward stores each step's exit face so that the
-backward replays the walk instead of searching the faces again.  The
-forward outputs must not change, and the gradients must equal those of the
+"""Walk record: the forward stores each step's segment (exit neighbour, exit
+parameter, density, colour before the clamp) so that the backward rebuilds
+the walk instead of reading the faces and attributes again.  The forward
+outputs must not change, and the gradients must equal those of the
 searching backward (the same exits, the same arithmetic; only the order of
 the floating-point atomics may differ)."""
 import numpy as np
