@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c1"])
     ap.add_argument("--sites", type=int, default=0, help="override the workload's site count")
+    ap.add_argument("--crop", default="", metavar="WxH",
+                    help="render only the centre WxH window of the workload's frame (the same rays as "
+                         "those pixels of the full frame; for profiler captures of a smaller case)")
     ap.add_argument("--no-extras", action="store_true", help="skip dtype variants / serving")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjacency-only", action="store_true",
@@ -76,6 +79,18 @@ def rank_camera(workload, rank):
     c2w = cam.c2w.astype(np.float64).copy()
     c2w[:, :3] = R @ c2w[:, :3]
     return S.Camera(c2w, cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.t_near, cam.t_far)
+
+
+def crop_camera(cam, crop):
+    """The centre ``WxH`` window of ``cam``'s image as a camera of its own:
+    same pose and focal lengths, principal point shifted by the window's
+    offset, so each of its rays is the full frame's ray through that pixel."""
+    from paper_2502_01157_gb300 import scenes as S
+
+    w, h = (int(v) for v in crop.lower().split("x"))
+    w, h = min(w, cam.width), min(h, cam.height)
+    x0, y0 = (cam.width - w) // 2, (cam.height - h) // 2
+    return S.Camera(cam.c2w, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, w, h, cam.t_near, cam.t_far)
 
 
 def bytes_per_step(k_bar, deg, attr_bytes):
@@ -329,7 +344,7 @@ def effects_extras(S, rf, foam, cam, target, scale, loss, grads, args, dev):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     res = {"recipe": "c3 scene, 1920x1080: fisheye 200 deg; rolling shutter (0.02, 0, 0.01) over the "
                      "frame; glass (n = 1.5) / mirror sphere r = 0.25 at 0.5 along the view axis; the "
-                     f"training step replays a {RECORD_STEPS}-step walk record"}
+                     f"training step rebuilds its backward walk from a {RECORD_STEPS}-step segment record"}
     # the training step keeps the forward's walk record, as the headline step does
     tout = dict(out, walk_record=(torch.empty(rf.walk_record_bytes([cam], RECORD_STEPS), dtype=torch.uint8,
                                               device=dev), RECORD_STEPS))
@@ -711,6 +726,8 @@ def main():
     # scene generation uses a spawn process pool: do it before CUDA starts
     scene = S.config_scene(args.workload, n_sites=args.sites or None)
     cam = rank_camera(args.workload, rank)
+    if args.crop:
+        cam = crop_camera(cam, args.crop)
     target_np = S.random_target(cam.n_rays, 2024 + rank)
     mix_scene = c1_scene = c2_scene = None
     if not args.no_extras and world == 1:
@@ -933,11 +950,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}"
-                                   + (f" (with {scene.n_sites} sites)" if args.sites else ""),
+                                   + (f" (with {scene.n_sites} sites)" if args.sites else "")
+                                   + (f" (centre {cam.width}x{cam.height} window only)" if args.crop else ""),
                        "n_sites": scene.n_sites, "n_edges": scene.n_edges, "rays_per_step": R,
                        "cell_steps_per_ray": steps_total / R, "sh_degree": deg,
-                       "step": f"fwd + mse grad + bwd (FP32 attributes; the backward replays a "
-                               f"{RECORD_STEPS}-step walk record of the forward)",
+                       "step": f"fwd + mse grad + bwd (FP32 attributes; the backward rebuilds its walk "
+                               f"from a {RECORD_STEPS}-step segment record of the forward)",
                        "l2": "inputs larger than L2 (packed foam %.2f GB)" % (foam.info()["device_bytes"] / 1e9),
                        "parallelism": f"dp{world}" if world > 1 else "single"},
             "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,

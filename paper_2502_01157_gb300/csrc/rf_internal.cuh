@@ -418,6 +418,22 @@ __device__ __forceinline__ uint32_t *record_column(const RenderParams &p) {
            (threadIdx.x & 31);
 }
 
+// The backward brings its warp's record rows into L2 kRecAhead steps ahead
+// of their loads, kRecAhead rows (contiguous, 768 bytes each) per bulk
+// prefetch issued by one lane: the record was written long before, so
+// without it every step's loads wait for DRAM.
+constexpr int kRecAhead = 8;
+
+// Prefetch the rows of steps [k, min(k + n, p.rec_steps)) of this warp's record.
+__device__ __forceinline__ void record_prefetch(const RenderParams &p, int k, int n) {
+    if (!p.rec || k >= p.rec_steps) return;
+    if (k + n > p.rec_steps) n = p.rec_steps - k;
+    const uint32_t *row = p.rec + ((int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5)) * p.rec_steps *
+                                      (32 * kRecWords) +
+                          (int64_t)k * (32 * kRecWords);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(row), "r"(n * 32 * kRecWords * 4) : "memory");
+}
+
 __device__ __forceinline__ void record_store(uint32_t *col, int k, const Segment &g) {
     uint32_t *r = col + (int64_t)k * (32 * kRecWords);
     __stcs(reinterpret_cast<int *>(r), g.next);

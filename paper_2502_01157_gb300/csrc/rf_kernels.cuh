@@ -231,6 +231,8 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
     if constexpr (FX) fx_begin(p.fx, o, d, f);
     // the forward's segment record of this warp (lane column), if given
     const uint32_t *rec = record_column(p);
+    if (kRecAhead > 0 && rec && lane == 0) record_prefetch(p, 0, 2 * kRecAhead);
+    int it = 0;  // warp iteration: step k of a live lane is iteration k
     float t0 = 0.f, T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
     int steps = 0;
     // the crossing that entered the current cell: (pa -> i) at pt; its adjoint
@@ -244,6 +246,10 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
     float dt = 0.f;
 
     while (__any_sync(full, live)) {
+        if constexpr (kRecAhead > 0) {
+            if (rec && lane == 0 && it > 0 && it % kRecAhead == 0) record_prefetch(p, it + kRecAhead, kRecAhead);
+        }
+        ++it;
         // stop tests of Alg. 1 (before the step); a crossing still pending
         // (T fell to eps right after it) is scattered by this lane alone
         if (live && (!(T > p.eps) || steps >= p.max_steps)) {
