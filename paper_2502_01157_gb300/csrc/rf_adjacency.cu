@@ -2,7 +2,10 @@
 // walk of Alg. 1 traverses (the Delaunay neighbour lists, rebuilt whenever the
 // sites move: the "Voronoi optimization" paragraph of Sec. 4).
 //
-// Each site's cell is built directly, one warp per site, as a convex polytope:
+// The method is the per-cell clipping of Ray, Sokolov, Lefebvre and Levy,
+// "Meshless Voronoi on the GPU" (ACM TOG 2018), written here from that
+// description.  Each site's cell is built directly, one warp per site, as a
+// convex polytope:
 // the domain box cut by the bisector half-spaces of nearby sites,
 //   (p_k - p_i) . x <= |p_k - p_i|^2 / 2   (x relative to p_i).
 // The polytope is kept in shared memory in dual form: every vertex is a
