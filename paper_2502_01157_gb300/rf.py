@@ -390,8 +390,10 @@ class Foam:
         status; + quantile [R] and quantile_aux [R,5] with ``quantile``) as
         CUDA tensors, rays of the cameras concatenated.  ``effects``: an
         analytic sphere the rays reflect off or refract through.  ``record``
-        > 0: also keep a walk record of that many steps per ray
-        (``out["walk_record"]``), which lets :meth:`backward` replay the walk."""
+        > 0: also keep a segment record of that many steps per ray
+        (``out["walk_record"]``, 24 bytes per step), which lets
+        :meth:`backward` rebuild the walk without the face search and the
+        attribute reads."""
         ca = camera_array(cams)
         R = n_rays_of(cams)
         dev = self.pos.device
@@ -426,9 +428,9 @@ class Foam:
         """Accumulate gradients (density, sh, pos; float32) of the forward
         outputs (and of the quantile loss, with ``d_quantile``) into ``grads``
         (zero-initialised if None).  A ``fwd`` that holds a ``walk_record``
-        is replayed instead of searched again.  The first backward that asks
-        for density or position gradients allocates a 16-byte-per-site
-        workspace owned by the scene."""
+        (a segment record) has its walk rebuilt from it instead of searched
+        again.  The first backward that asks for density or position
+        gradients allocates a 16-byte-per-site workspace owned by the scene."""
         if grads is None:
             dev = self.pos.device
             grads = dict(density=torch.zeros(self.n_sites, device=dev),
@@ -677,8 +679,10 @@ def render(foam: Foam, cams, density=None, sh=None, pos=None, eps: float = 1e-4,
     depth [R]) and, with ``quantile``, the per-ray quantile loss of Eq. (6)
     [R]; gradients flow to ``density``, ``sh`` and ``pos`` (defaults: the
     foam's own tensors).  A changed ``pos`` is re-packed first.  ``record``:
-    steps per ray of the walk record kept between the passes (0: none; the
-    backward then searches every step's exit again)."""
+    steps per ray of the segment record kept between the passes, 24 bytes per
+    step for every ray slot of the cameras' 16x8 tiles (12.7 GB for a
+    1920x1080 frame at 256 steps); 0: none, the backward then searches every
+    step's exit again and re-reads the attributes."""
     density = foam.density if density is None else density
     sh = foam.sh if sh is None else sh
     if density is not foam.density or sh is not foam.sh:

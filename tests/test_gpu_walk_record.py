@@ -114,6 +114,34 @@ def test_short_record_buffer_is_rejected():
         foam.render([cam], out=out)
 
 
+def test_unaligned_record_buffer_is_rejected():
+    sc = random_scene(800, 0, 54)
+    foam = foam_of(sc)
+    cam = camera_at((0.0, 0.0, 0.0), (1.0, 0.0, 0.0), w=20, h=10)
+    out = foam.render([cam], record=8)
+    buf, steps = out["walk_record"]
+    out["walk_record"] = (buf[4:], steps)   # 4 bytes past a 16-byte boundary
+    with pytest.raises(rf.RFError, match="aligned"):
+        foam.render([cam], out=out)
+
+
+def test_record_of_another_scene_stays_in_bounds():
+    """A record made on a larger scene holds exit ids beyond the smaller
+    scene's sites: the backward ends those walks instead of following them
+    (the gradients are not meaningful, but every access stays in bounds and
+    the call succeeds)."""
+    big = foam_of(random_scene(3000, 1, 61))
+    small = foam_of(random_scene(500, 1, 62))
+    cam = camera_at((0.05, 0.1, -0.02), (0.2, -0.3, 1.0), w=40, h=24)
+    out = big.render([cam], record=64)
+    ids = out["walk_record"][0].view(torch.int32).view(-1, 6, 32)[:, 0, :]
+    assert int(ids.max()) >= 500   # the record does name sites the small scene lacks
+    gr = torch.randn_like(out["rgb"])
+    G = small.backward([cam], out, gr)
+    torch.cuda.synchronize()   # the launch completed without a fault
+    assert G["density"].shape == (500,) and G["pos"].shape == (500, 3)
+
+
 def test_full_size_c3_replay():
     sc = S.config_scene("c3")
     cam = S.config_cameras("c3")[0]
