@@ -150,7 +150,7 @@ struct BwdIO {
 // g_density.  The rows of lanes alone in their cell are spread over the warp,
 // one 16-byte column per lane.  The crossing that entered the cell also moves
 // the previous cell's site; each lane adds those three terms to g_acc itself.
-constexpr int kMaxGroups = 12;
+constexpr int kMaxGroups = 8;
 
 template <typename AT, int DEG, bool QUANT, bool FX>
 __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, const BwdIO io) {
@@ -421,12 +421,15 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
             constexpr int NQ = VP / 4;
             constexpr int SQ = SP / 4;
             const float4 *stage4 = reinterpret_cast<const float4 *>(stage);
-            // column c (floats 4c .. 4c+3) of a row of `cell` into the gradients
+            // column c (floats 4c .. 4c+3) of a row of `cell` into the
+            // gradients that were asked for (a zero column is added too:
+            // testing for it costs more than the rare empty atomic)
             auto add_column = [&](int cell, int col, const float4 &v) {
                 const int c = 4 * col;
-                if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) return;
                 if (c >= NVP) {
-                    atomicAdd(io.g_acc + cell, v);   // {position, density} of the cell
+                    if (io.g_acc) atomicAdd(io.g_acc + cell, v);   // {position, density} of the cell
+                } else if (!io.g_sh) {
+                    // no SH gradient wanted
                 } else if (NV % 4 == 0 && io.sh_vec) {
                     atomicAdd(reinterpret_cast<float4 *>(io.g_sh + (size_t)cell * NV + c), v);
                 } else {
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                 const unsigned m = __shfl_sync(full, peers, L);
                 const int cell_i = __shfl_sync(full, i, L);
                 if ((lane < 16 || two) && hl < NQ) {
-                    // four members per trip with independent loads; an absent
+                    // three members per trip with independent loads; an absent
                     // member (-1) loads nothing
                     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
                     float4 sm = z4;
@@ -460,23 +463,19 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
                         mm &= mm - 1;
                         const int k2 = __ffs(mm) - 1;
                         mm &= mm - 1;
-                        const int k3 = __ffs(mm) - 1;
-                        mm &= mm - 1;
                         const float4 a0 = stage4[k0 * SQ + hl];
-                        float4 a1, a2, a3;
+                        float4 a1, a2;
                         if constexpr (FX) {
                             a1 = stage4[(k1 >= 0 ? k1 : 32) * SQ + hl];
                             a2 = stage4[(k2 >= 0 ? k2 : 32) * SQ + hl];
-                            a3 = stage4[(k3 >= 0 ? k3 : 32) * SQ + hl];
                         } else {
                             a1 = k1 >= 0 ? stage4[k1 * SQ + hl] : z4;
                             a2 = k2 >= 0 ? stage4[k2 * SQ + hl] : z4;
-                            a3 = k3 >= 0 ? stage4[k3 * SQ + hl] : z4;
                         }
-                        sm.x += (a0.x + a1.x) + (a2.x + a3.x);
-                        sm.y += (a0.y + a1.y) + (a2.y + a3.y);
-                        sm.z += (a0.z + a1.z) + (a2.z + a3.z);
-                        sm.w += (a0.w + a1.w) + (a2.w + a3.w);
+                        sm.x += (a0.x + a1.x) + a2.x;
+                        sm.y += (a0.y + a1.y) + a2.y;
+                        sm.z += (a0.z + a1.z) + a2.z;
+                        sm.w += (a0.w + a1.w) + a2.w;
                     }
                     add_column(cell_i, hl, sm);
                 }
