@@ -840,6 +840,24 @@ def main():
         barrier()
         fwd_only = R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
         res["fwd_fp32_mrays_s"] = fwd_only
+        # the same training step by pure recomputation: no segment record, the
+        # backward searches every exit again and re-reads density and SH
+
+        def rstep():
+            foam.render([cam], out=out_fwd)
+            d_rgb, _ = rf.mse_grad(out_fwd["rgb"], target, scale, loss)
+            foam.backward([cam], out_fwd, d_rgb, grads=grads)
+
+        for _ in range(2):
+            rstep()
+        barrier()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(args.steps):
+            rstep()
+        b.record()
+        barrier()
+        res["fwdbwd_recompute_fp32_mrays_s"] = R / (a.elapsed_time(b) / args.steps * 1e-3) / 1e6
         # attribute storage variants (same geometry, own copies of the attributes)
         for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16)):
             d2 = torch.from_numpy(scene.density).to(dev, dt)
