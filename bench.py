@@ -114,14 +114,19 @@ L1_BYTES_PER_CLK = 128   # L1 load data path: one 128-byte wavefront per clock p
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources the renderer's kernels are built from."""
+    """Hash of the CUDA sources the renderer's kernels are built from, with
+    comments removed and white space collapsed (a comment edit keeps the
+    counters measured on the same code)."""
     import hashlib
+    import re
 
+    tok = re.compile(r'("(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\')|//[^\n]*|/\*.*?\*/', re.S)
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2502_01157_gb300", "csrc")
     for name in ("rf_host.h", "rf_internal.cuh", "rf_kernels.cuh", "rf_render.cu", "rf_scene.cu"):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            code = tok.sub(lambda m: m.group(1) or " ", f.read())
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:12]
 
 

@@ -135,9 +135,12 @@ struct BwdIO {
     const float *qaux, *d_quantile;
 };
 
-// Backward: the walk of the forward is repeated with identical arithmetic;
-// per segment the adjoints follow from the stored final colour, transmittance
-// and depth (C_rest = C_final - C_incl).
+// Backward: every ray is walked again, step by step.  A step the forward's
+// segment record holds is rebuilt from it (exit, density, colour before the
+// clamp); any other step (all of them without a record) searches the faces
+// and reads the attributes with the forward's arithmetic, so both meet the
+// same bits.  Per segment the adjoints follow from the stored final colour,
+// transmittance and depth (C_rest = C_final - C_incl).
 //
 // Scatter.  Neighbouring rays of a warp mostly walk the same cells (a warp of
 // an 8x4 patch meets ~5-7 distinct cells per iteration at 1920x1080 and reuses
