@@ -561,9 +561,42 @@ def workload_extras(rf, scene, cam, args, dev, name):
     torch.cuda.synchronize()
     fwd_ms = a.elapsed_time(b) / n
     step_ms = b.elapsed_time(c) / n
+    # the same calls replayed from CUDA graphs, each captured once: a small
+    # frame is launch-bound, and a replay issues the calls' memsets and kernels
+    # without the host's per-call work
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            foam.render([cam], out=out)
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g_fwd, g_step = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_fwd):
+        foam.render([cam], out=out)
+    with torch.cuda.graph(g_step):
+        step()
+    for _ in range(3):
+        g_fwd.replay()
+        g_step.replay()
+    torch.cuda.synchronize()
+    a, b, c = ev(), ev(), ev()
+    a.record()
+    for _ in range(n):
+        g_fwd.replay()
+    b.record()
+    for _ in range(n):
+        g_step.replay()
+    c.record()
+    torch.cuda.synchronize()
+    gfwd_ms = a.elapsed_time(b) / n
+    gstep_ms = b.elapsed_time(c) / n
     k_bar = scene.n_edges / scene.n_sites
     fb = bytes_per_step(k_bar, deg, 4)
     res = {"workload": f"{name}: {WORKLOADS[name]['desc']}", "rays": R, "n_sites": scene.n_sites,
+           "graph_fwd_ms": gfwd_ms, "graph_fwd_mrays_s": R / gfwd_ms / 1e3,
+           "graph_fwdbwd_ms": gstep_ms, "graph_fwdbwd_mrays_s": R / gstep_ms / 1e3,
            "cell_steps_per_ray": steps_total / R, "iterations": n,
            "fwd_ms": fwd_ms, "fwd_mrays_s": R / fwd_ms / 1e3, "fwd_cell_steps_per_s": steps_total / fwd_ms * 1e3,
            "fwdbwd_ms": step_ms, "fwdbwd_mrays_s": R / step_ms / 1e3,
