@@ -447,16 +447,17 @@ def mixture_extras(scene, args, dev):
     tout = dict(out, walk_record=(torch.empty(rf.walk_record_bytes(cams, RECORD_STEPS), dtype=torch.uint8,
                                               device=dev), RECORD_STEPS))
 
-    def step():
+    def step(shared=True):
         foam.render(cams, out=tout)
         d, _ = rf.mse_grad(tout["rgb"], target, 1.0 / (3 * R))
-        foam.backward(cams, tout, d, grads=grads)
+        foam.backward(cams, tout, d, grads=grads, shared_cells=shared)
 
     for _ in range(2):
         step()
+        step(False)
     torch.cuda.synchronize()
     n = max(3, args.steps // 2)
-    a, b, c = ev(), ev(), ev()
+    a, b, c, e = ev(), ev(), ev(), ev()
     a.record()
     for _ in range(n):
         foam.render(cams, out=out)
@@ -464,12 +465,17 @@ def mixture_extras(scene, args, dev):
     for _ in range(n):
         step()
     c.record()
+    for _ in range(n):
+        step(False)
+    e.record()
     torch.cuda.synchronize()
     res = {"scene": f"c4/c5 mixture, {scene.n_sites} sites, SH deg 3",
            "c4_cameras": "8 mixed (2x 640x480, 1280x720, 1600x900, 1920x1080) on a radius-12 sphere",
            "c4_rays": R,
            "c4_fwd_fp32_mrays_s": R * n / (a.elapsed_time(b) * 1e-3) / 1e6,
-           "c4_fwdbwd_fp32_mrays_s": R * n / (b.elapsed_time(c) * 1e-3) / 1e6}
+           "c4_fwdbwd_fp32_mrays_s": R * n / (b.elapsed_time(c) * 1e-3) / 1e6,
+           "c4_fwdbwd_backward": "shared-cell backward (RF_RENDER_SHARED_CELLS)",
+           "c4_fwdbwd_default_backward_fp32_mrays_s": R * n / (c.elapsed_time(e) * 1e-3) / 1e6}
     # serving poses and resolutions; batched forward of 16 of them, FP32 vs BF16
     rng = np.random.default_rng(1005)
     bposes = S.sphere_poses(16, 12.0, 1006)
@@ -520,10 +526,12 @@ def mixture_extras(scene, args, dev):
     return res
 
 
-def workload_extras(rf, scene, cam, args, dev, name):
+def workload_extras(rf, scene, cam, args, dev, name, shared_cells=False):
     """Throughput of another workload in the headline step's launch
     configuration: forward alone and the training step (forward with a walk
-    record, MSE gradient, replayed backward), with cell steps and bytes."""
+    record, MSE gradient, replayed backward), with cell steps and bytes.
+    ``shared_cells``: the training step uses the shared-cell backward (the
+    default backward is timed beside it)."""
     import torch
 
     R = cam.n_rays
@@ -540,10 +548,10 @@ def workload_extras(rf, scene, cam, args, dev, name):
     steps_total = int(foam.render([cam], steps=True)["steps"].sum().item())
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step():
+    def step(shared=shared_cells):
         foam.render([cam], out=tout)
         d, _ = rf.mse_grad(tout["rgb"], target, 1.0 / (3 * R))
-        foam.backward([cam], tout, d, grads=grads)
+        foam.backward([cam], tout, d, grads=grads, shared_cells=shared)
 
     # a small frame is launch-bound: time enough iterations for ~0.2 s
     n = max(args.steps, int(2e7 // max(R, 1)))
@@ -561,6 +569,18 @@ def workload_extras(rf, scene, cam, args, dev, name):
     torch.cuda.synchronize()
     fwd_ms = a.elapsed_time(b) / n
     step_ms = b.elapsed_time(c) / n
+    default_step_ms = None
+    if shared_cells:
+        for _ in range(2):
+            step(False)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(n):
+            step(False)
+        b.record()
+        torch.cuda.synchronize()
+        default_step_ms = a.elapsed_time(b) / n
     # the same calls replayed from CUDA graphs, each captured once: a small
     # frame is launch-bound, and a replay issues the calls' memsets and kernels
     # without the host's per-call work
@@ -595,6 +615,8 @@ def workload_extras(rf, scene, cam, args, dev, name):
     k_bar = scene.n_edges / scene.n_sites
     fb = bytes_per_step(k_bar, deg, 4)
     res = {"workload": f"{name}: {WORKLOADS[name]['desc']}", "rays": R, "n_sites": scene.n_sites,
+           "backward": "shared-cell backward (RF_RENDER_SHARED_CELLS)" if shared_cells else "default backward",
+           "fwdbwd_default_backward_mrays_s": R / default_step_ms / 1e3 if default_step_ms else None,
            "graph_fwd_ms": gfwd_ms, "graph_fwd_mrays_s": R / gfwd_ms / 1e3,
            "graph_fwdbwd_ms": gstep_ms, "graph_fwdbwd_mrays_s": R / gstep_ms / 1e3,
            "cell_steps_per_ray": steps_total / R, "iterations": n,
@@ -945,7 +967,8 @@ def main():
         res["adjacency"] = adjacency_extras(rf, scene, mix_scene, args, dev)
         for name, sc in (("c1", c1_scene), ("c2", c2_scene)):
             if sc is not None and name != args.workload:
-                res[f"{name}_gpu"] = workload_extras(rf, sc, S.config_cameras(name)[0], args, dev, name)
+                res[f"{name}_gpu"] = workload_extras(rf, sc, S.config_cameras(name)[0], args, dev, name,
+                                                     shared_cells=name == "c2")
 
     mixture = None
     if mix_scene is not None:

@@ -6,6 +6,6 @@
 namespace rf {
 
 template void launch_fwd_any<true>(int, int, int, int64_t, const RenderParams &, const FwdOut &, cudaStream_t);
-template void launch_bwd_any<true>(int, int, bool, int64_t, const RenderParams &, const BwdIO &, cudaStream_t);
+template void launch_bwd_any<true, false>(int, int, bool, int64_t, const RenderParams &, const BwdIO &, cudaStream_t);
 
 }  // namespace rf

@@ -155,7 +155,15 @@ struct BwdIO {
 // the previous cell's site; each lane adds those three terms to g_acc itself.
 constexpr int kMaxGroups = 8;
 
-template <typename AT, int DEG, bool QUANT, bool FX>
+// SHARED: the crossing terms of the previous cell (below) are summed over the
+// lanes that share that cell before their atomic, in warp iterations whose
+// live lanes are in at most kSharedCells distinct cells.  Where many rays cross
+// the same cells (large cells, cameras far from the foam) this removes most
+// same-address atomics, which the L2 serialises; on dense foams (~4 lanes per
+// cell) the extra code costs more than it saves, so it is a separate kernel.
+constexpr int kSharedCells = 2;
+
+template <typename AT, int DEG, bool QUANT, bool FX, bool SHARED>
 __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, const BwdIO io) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int NV = 3 * K;              // SH gradient row
@@ -385,14 +393,41 @@ __global__ void __launch_bounds__(kBlock, 6) bwd_kernel(const RenderParams p, co
         // ---- warp-wide scatter of this iteration's contributions ----
         // The crossing that entered the cell also moves the previous cell's
         // site: each lane adds those three terms itself.
-        if (live && key_prev >= 0 && (gpos_a[0] != 0.f || gpos_a[1] != 0.f || gpos_a[2] != 0.f))
-            atomicAdd(io.g_acc + key_prev, make_float4(gpos_a[0], gpos_a[1], gpos_a[2], 0.f));
+        if constexpr (!SHARED) {
+            if (live && key_prev >= 0 && (gpos_a[0] != 0.f || gpos_a[1] != 0.f || gpos_a[2] != 0.f))
+                atomicAdd(io.g_acc + key_prev, make_float4(gpos_a[0], gpos_a[1], gpos_a[2], 0.f));
+        }
         // The rest goes to the current cell.  Lanes in the same cell are
         // summed over 16-byte columns of their staged rows, two cells per
         // pass; the rows of lanes alone in their cell (or of every lane, when
         // the warp is spread over more than kMaxGroups shared cells) are
         // spread over the whole warp, one (row, column) item per lane.
         const unsigned peers = __match_any_sync(full, live ? (unsigned)i : 0xffffffffu);
+        if constexpr (SHARED) {
+            // the previous cells' crossing terms, summed per cell when the
+            // warp's lanes share few cells, else added lane by lane
+            __shared__ float4 cross_all[kBlock / 32][32];
+            const int ncell = __popc(__ballot_sync(full, live && lane == __ffs(peers) - 1));
+            const bool has_a = live && key_prev >= 0 && (gpos_a[0] != 0.f || gpos_a[1] != 0.f || gpos_a[2] != 0.f);
+            if (ncell > kSharedCells) {
+                if (has_a) atomicAdd(io.g_acc + key_prev, make_float4(gpos_a[0], gpos_a[1], gpos_a[2], 0.f));
+            } else {
+                float4 *cross = cross_all[threadIdx.x >> 5];
+                const unsigned am = __match_any_sync(full, has_a ? (unsigned)key_prev : 0xffffffffu);
+                if (has_a) cross[lane] = make_float4(gpos_a[0], gpos_a[1], gpos_a[2], 0.f);
+                __syncwarp();
+                if (has_a && lane == __ffs(am) - 1) {
+                    float4 sm = cross[lane];
+                    for (unsigned mm = am & (am - 1); mm; mm &= mm - 1) {
+                        const float4 v = cross[__ffs(mm) - 1];
+                        sm.x += v.x;
+                        sm.y += v.y;
+                        sm.z += v.z;
+                    }
+                    atomicAdd(io.g_acc + key_prev, sm);
+                }
+            }
+        }
         const bool in_group = live && __popc(peers) > 1;
         unsigned leaders = __ballot_sync(full, in_group && lane == __ffs(peers) - 1);
         if (__popc(leaders) > kMaxGroups) leaders = 0u;
@@ -539,12 +574,12 @@ void launch_fwd_any(int dtype, int deg, int mode, int64_t tiles, const RenderPar
     });
 }
 
-template <bool FX>
+template <bool FX, bool SHARED>
 void launch_bwd_any(int dtype, int deg, bool quant, int64_t tiles, const RenderParams &p, const BwdIO &io,
                     cudaStream_t st) {
     dispatch(dtype, deg, [&]<typename AT, int DEG>() {
-        if (quant) bwd_kernel<AT, DEG, true, FX><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
-        else bwd_kernel<AT, DEG, false, FX><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
+        if (quant) bwd_kernel<AT, DEG, true, FX, SHARED><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
+        else bwd_kernel<AT, DEG, false, FX, SHARED><<<(unsigned)tiles, kBlock, 0, st>>>(p, io);
     });
 }
 
@@ -552,9 +587,13 @@ extern template void launch_fwd_any<false>(int, int, int, int64_t, const RenderP
                                            cudaStream_t);
 extern template void launch_fwd_any<true>(int, int, int, int64_t, const RenderParams &, const FwdOut &,
                                           cudaStream_t);
-extern template void launch_bwd_any<false>(int, int, bool, int64_t, const RenderParams &, const BwdIO &,
-                                           cudaStream_t);
-extern template void launch_bwd_any<true>(int, int, bool, int64_t, const RenderParams &, const BwdIO &,
-                                          cudaStream_t);
+extern template void launch_bwd_any<false, false>(int, int, bool, int64_t, const RenderParams &, const BwdIO &,
+                                                  cudaStream_t);
+extern template void launch_bwd_any<true, false>(int, int, bool, int64_t, const RenderParams &, const BwdIO &,
+                                                 cudaStream_t);
+extern template void launch_bwd_any<false, true>(int, int, bool, int64_t, const RenderParams &, const BwdIO &,
+                                                 cudaStream_t);
+extern template void launch_bwd_any<true, true>(int, int, bool, int64_t, const RenderParams &, const BwdIO &,
+                                                cudaStream_t);
 
 }  // namespace rf

@@ -9,7 +9,7 @@
 namespace rf {
 
 template void launch_fwd_any<false>(int, int, int, int64_t, const RenderParams &, const FwdOut &, cudaStream_t);
-template void launch_bwd_any<false>(int, int, bool, int64_t, const RenderParams &, const BwdIO &, cudaStream_t);
+template void launch_bwd_any<false, false>(int, int, bool, int64_t, const RenderParams &, const BwdIO &, cudaStream_t);
 
 // The effects kernels run when the launch has a sphere, a fisheye camera or
 // a rolling shutter.
@@ -29,10 +29,15 @@ static void launch_fwd_fx(const RenderParams &p, int dtype, int deg, int mode, i
     else launch_fwd_any<false>(dtype, deg, mode, tiles, p, o, st);
 }
 
-static void launch_bwd_fx(const RenderParams &p, int dtype, int deg, bool quant, int64_t tiles,
+static void launch_bwd_fx(const RenderParams &p, int dtype, int deg, bool quant, bool shared, int64_t tiles,
                           const BwdIO &io, cudaStream_t st) {
-    if (needs_fx(p)) launch_bwd_any<true>(dtype, deg, quant, tiles, p, io, st);
-    else launch_bwd_any<false>(dtype, deg, quant, tiles, p, io, st);
+    if (needs_fx(p)) {
+        if (shared) launch_bwd_any<true, true>(dtype, deg, quant, tiles, p, io, st);
+        else launch_bwd_any<true, false>(dtype, deg, quant, tiles, p, io, st);
+    } else {
+        if (shared) launch_bwd_any<false, true>(dtype, deg, quant, tiles, p, io, st);
+        else launch_bwd_any<false, false>(dtype, deg, quant, tiles, p, io, st);
+    }
 }
 
 __global__ void mse_grad_kernel(const float *__restrict__ rgb, const float *__restrict__ target,
@@ -244,7 +249,8 @@ RF_API rf_status rf_render_bwd_ex(rf_scene *s, const rf_camera *cams, int32_t n_
         p.rec = in->walk_record ? reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(in->walk_record) + rec_off)
                                 : nullptr;
         if (in->walk_record) rec_off += record_bytes_of(cams, first, count, in->walk_record_steps);
-        launch_bwd_fx(p, s->attr_dtype, s->sh_degree, quant, tiles, io, st);
+        launch_bwd_fx(p, s->attr_dtype, s->sh_degree, quant, opts && (opts->flags & RF_RENDER_SHARED_CELLS), tiles,
+                      io, st);
         RF_CUDA(cudaGetLastError());
     }
     if (acc) {

@@ -77,6 +77,7 @@ rf_status check_opts(const rf_render_opts *o, float *eps, int32_t *max_steps, Sp
         if (!(o->eps >= 0.f) || !std::isfinite(o->eps))
             return fail(RF_ERR_INVALID_ARG, "opts.eps must be finite and >= 0");
         *eps = o->eps;
+        if (o->flags & ~RF_RENDER_SHARED_CELLS) return fail(RF_ERR_INVALID_ARG, "unknown bits in opts.flags");
         if (o->max_steps > 0) *max_steps = o->max_steps;
         if (o->max_bounces < 0) return fail(RF_ERR_INVALID_ARG, "opts.max_bounces must be >= 0");
         if (o->max_bounces > 0) {

@@ -234,12 +234,18 @@ def walk_record_bytes(cams, steps: int) -> int:
     return int(lib().rf_walk_record_bytes(ca, len(ca), int(steps)))
 
 
-def opts_struct(eps: float = 1e-4, max_steps: int = 0, effects=None) -> rf_render_opts:
+RF_RENDER_SHARED_CELLS = 1
+
+
+def opts_struct(eps: float = 1e-4, max_steps: int = 0, effects=None, shared_cells: bool = False) -> rf_render_opts:
     """Render options; ``effects`` is an analytic sphere with ``centre``,
-    ``radius``, ``ior`` (0: mirror) and ``max_bounces`` (e.g. ``scenes.Sphere``)."""
+    ``radius``, ``ior`` (0: mirror) and ``max_bounces`` (e.g. ``scenes.Sphere``);
+    ``shared_cells`` selects the backward for frames whose rays share cells
+    heavily (``RF_RENDER_SHARED_CELLS``)."""
     o = rf_render_opts()
     o.eps = float(eps)
     o.max_steps = int(max_steps)
+    o.flags = RF_RENDER_SHARED_CELLS if shared_cells else 0
     if effects is not None:
         o.max_bounces = int(effects.max_bounces)
         o.sphere[:] = [float(v) for v in effects.centre] + [float(effects.radius)]
@@ -424,20 +430,22 @@ class Foam:
 
     def backward(self, cams, fwd: dict, d_rgb, d_trans=None, d_depth=None, grads=None,
                  eps: float = 1e-4, max_steps: int = 0, d_quantile=None, stream=None,
-                 effects=None) -> dict:
+                 effects=None, shared_cells: bool = False) -> dict:
         """Accumulate gradients (density, sh, pos; float32) of the forward
         outputs (and of the quantile loss, with ``d_quantile``) into ``grads``
         (zero-initialised if None).  A ``fwd`` that holds a ``walk_record``
         (a segment record) has its walk rebuilt from it instead of searched
         again.  The first backward that asks for density or position
-        gradients allocates a 16-byte-per-site workspace owned by the scene."""
+        gradients allocates a 16-byte-per-site workspace owned by the scene.
+        ``shared_cells``: the backward for frames whose rays share cells
+        heavily (``RF_RENDER_SHARED_CELLS``)."""
         if grads is None:
             dev = self.pos.device
             grads = dict(density=torch.zeros(self.n_sites, device=dev),
                          sh=torch.zeros(tuple(self.sh.shape), device=dev),
                          pos=torch.zeros(self.n_sites, 3, device=dev))
         ca = camera_array(cams)
-        o = opts_struct(eps, max_steps, effects)
+        o = opts_struct(eps, max_steps, effects, shared_cells)
         rec = fwd.get("walk_record")
         bi = rf_bwd_inputs(_addr(fwd["rgb"]), _addr(fwd["trans"]), _addr(fwd.get("depth")),
                            _addr(fwd.get("quantile_aux")), _addr(d_rgb), _addr(d_trans),

@@ -128,6 +128,19 @@ def compare_traces(cells_gpu, counts_gpu, orc, max_per_ray):
     return bad, int(tie.sum())
 
 
+def assert_same_sums(a, b, tag=""):
+    """Two GPU gradients that differ only in the order of their float atomics:
+    relative L2 within 2e-6, and each element within 1e-5 of the tensor's
+    largest magnitude (a sum with cancellation can differ by more than 1e-5
+    of its own value, so no element-wise relative bound is used)."""
+    a = np.asarray(a.detach().cpu() if hasattr(a, "detach") else a, np.float64)
+    b = np.asarray(b.detach().cpu() if hasattr(b, "detach") else b, np.float64)
+    e = rel_l2(a, b)
+    assert e <= 2e-6, (tag, e)
+    scale = float(np.max(np.abs(b))) if b.size else 0.0
+    assert np.all(np.abs(a - b) <= 1e-5 * scale + 1e-12), (tag, float(np.max(np.abs(a - b))), scale)
+
+
 def rel_l2(a, b):
     a = np.asarray(a, np.float64).reshape(-1)
     b = np.asarray(b, np.float64).reshape(-1)

@@ -9,7 +9,7 @@ import oracle
 from paper_2502_01157_gb300 import rf
 from paper_2502_01157_gb300 import scenes as S
 from tests.helpers import camera_at, random_scene
-from tests.parity import GRAD_REL, check_flag_fractions, foam_of, rel_l2, rounded_scene
+from tests.parity import assert_same_sums, GRAD_REL, check_flag_fractions, foam_of, rel_l2, rounded_scene
 
 pytestmark = pytest.mark.gpu
 Q_RMSE = 1e-5
@@ -95,8 +95,8 @@ def test_quantile_autograd_matches_direct_backward():
     fwd = foam.render([cam], quantile=True)
     G = foam.backward([cam], fwd, torch.ones_like(fwd["rgb"]),
                       d_quantile=torch.full_like(fwd["quantile"], 0.3))
-    torch.testing.assert_close(dens.grad, G["density"], rtol=1e-5, atol=1e-6)
-    torch.testing.assert_close(pos.grad, G["pos"], rtol=1e-5, atol=1e-6)
+    assert_same_sums(dens.grad, G["density"], "density")
+    assert_same_sums(pos.grad, G["pos"], "pos")
 
 
 def test_quantile_full_size_c3_sampled():

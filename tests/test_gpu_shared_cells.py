@@ -1,0 +1,94 @@
+"""The backward selected by RF_RENDER_SHARED_CELLS sums the previous cells'
+crossing terms over the lanes of a warp that share a cell before adding them.
+Its gradients must be those of the default backward up to the order of the
+float additions, and match the oracle's."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2502_01157_gb300 import rf
+from paper_2502_01157_gb300 import scenes as S
+from tests.helpers import camera_at, random_scene
+from tests.parity import GRAD_REL, foam_of, rel_l2
+from tests.test_gpu_parity import _bwd_compare
+
+pytestmark = pytest.mark.gpu
+SAME = 2e-6     # float atomics added in another order
+# a full frame: a hot cell's site terms sum up to ~1e5 crossings, and two
+# FP32 orders of such a sum differ by ~sqrt(n) x 2^-24 of its terms' size
+SAME_FULL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    rf.lib()
+
+
+def _both(foam, cams, out, gr, tol, **kw):
+    a = foam.backward(cams, out, gr, torch.full_like(out["trans"], 0.3), torch.full_like(out["depth"], 0.1), **kw)
+    b = foam.backward(cams, out, gr, torch.full_like(out["trans"], 0.3), torch.full_like(out["depth"], 0.1),
+                      shared_cells=True, **kw)
+    torch.cuda.synchronize()
+    for k in a:
+        e = rel_l2(b[k].cpu().numpy(), a[k].cpu().numpy())
+        print(f"{k} rel {e:.1e}")
+        assert e <= tol, (k, e)
+
+
+@pytest.mark.parametrize("n_sites,record", [(3000, 0), (3000, 384), (300, 64), (60, 0)])
+def test_shared_cells_equals_default(n_sites, record):
+    # few sites: large cells that whole warps share, so the summed path runs
+    sc = random_scene(n_sites, 3, 200 + n_sites)
+    foam = foam_of(sc)
+    cams = [camera_at((0.1, -0.05, 0.02), (0.3, 1.0, 0.2), w=67, h=45),
+            camera_at((2.2, 1.9, -1.4), (0.0, 0.0, 0.0), w=33, h=17)]
+    out = foam.render(cams, record=record)
+    _both(foam, cams, out, torch.randn_like(out["rgb"]), SAME)
+
+
+def test_shared_cells_with_effects_and_quantile():
+    sc = random_scene(400, 3, 51)
+    foam = foam_of(sc)
+    cams = [S.fisheye(31, 23, 200.0, c2w=S.look_at((-0.85, 0.3, 0.2), (0.1, 0.0, 0.05)))]
+    sph = S.Sphere((0.1, 0.0, 0.05), 0.3, ior=1.5, max_bounces=4)
+    out = foam.render(cams, quantile=True, effects=sph, record=64)
+    gq = torch.full_like(out["quantile"], 0.01)
+    _both(foam, cams, out, torch.randn_like(out["rgb"]), SAME, d_quantile=gq, effects=sph)
+
+
+def test_shared_cells_matches_oracle():
+    sc = random_scene(400, 3, 11)
+    sc.sh[:, 1:, :] = np.random.default_rng(12).normal(0, 0.3, sc.sh[:, 1:, :].shape).astype(np.float32)
+    cams = [camera_at((0.1, -0.05, 0.02), (0.3, 1.0, 0.2), w=40, h=30),
+            camera_at((2.2, 1.9, -1.4), (0.0, 0.0, 0.0), w=24, h=16)]
+    errs = _bwd_compare(sc, cams, record=256, shared_cells=True)
+    print("shared cells vs oracle", errs)
+    for k, e in errs.items():
+        assert e <= GRAD_REL, (k, e)
+
+
+def test_unknown_flag_bits_are_rejected():
+    sc = random_scene(200, 0, 3)
+    foam = foam_of(sc)
+    cam = camera_at((0.0, 0.0, 0.0), (1.0, 0.0, 0.0), w=8, h=8)
+    o = rf.opts_struct()
+    o.flags = 2
+    out = dict(rgb=torch.empty(64, 3, device="cuda"), trans=torch.empty(64, device="cuda"),
+               depth=torch.empty(64, device="cuda"))
+    ca = rf.camera_array([cam])
+    st = rf.lib().rf_render_fwd(foam.handle, ca, 1, ctypes.byref(o), rf._ptr(out["rgb"]), rf._ptr(out["trans"]),
+                                rf._ptr(out["depth"]), None, None, None)
+    assert st == 1   # RF_ERR_INVALID_ARG
+
+
+def test_full_size_mixture_shared_cells():
+    # the 1M-site Gaussian mixture frame, where the summed path pays
+    sc = S.config_scene("c2")
+    cams = S.config_cameras("c2")
+    foam = foam_of(sc)
+    out = foam.render(cams, record=384)
+    _both(foam, cams, out, torch.randn_like(out["rgb"]) * 1e-3, SAME_FULL)
