@@ -55,7 +55,7 @@ def _check_traces(scene, foam, cam, dt="f32"):
     return bad_total, check_flag_fractions(np.concatenate(flags), FULL_SIZE_FLAG_BOUNDS)
 
 
-def _check_backward_sampled(scene, foam, cams, dt="f32", seed=1, record=0):
+def _check_backward_sampled(scene, foam, cams, dt="f32", seed=1, record=0, shared_cells=False):
     """Full launch; the loss weights only sampled, unflagged rays, so the
     oracle can compute the reference gradient.  ``record`` > 0: the backward
     replays the forward's walk record, as the timed training step does."""
@@ -77,7 +77,7 @@ def _check_backward_sampled(scene, foam, cams, dt="f32", seed=1, record=0):
         for k in ref_g:
             ref_g[k] += G[k]
         base += cam.n_rays
-    G = foam.backward(cams, fwd, torch.from_numpy(gr).cuda())
+    G = foam.backward(cams, fwd, torch.from_numpy(gr).cuda(), shared_cells=shared_cells)
     torch.cuda.synchronize()
     return {k: rel_l2(G[k].cpu().numpy(), ref_g[k]) for k in ref_g}
 

@@ -86,9 +86,26 @@ def test_unknown_flag_bits_are_rejected():
 
 
 def test_full_size_mixture_shared_cells():
-    # the 1M-site Gaussian mixture frame, where the summed path pays
+    """The 1M-site Gaussian-mixture frame, where the summed path pays: against
+    the oracle on sampled unflagged pixels, and against the default backward
+    on the whole frame for density and SH.  Positions are compared with the
+    oracle only: with every ray's adjoint set, grazing crossings (1/den) put
+    large terms of both signs into the hot cells' site sums, whose FP32 value
+    then depends on the summation order (3.4e-4 between the two backwards)."""
+    from tests.test_gpu_full import RECORD, _check_backward_sampled
     sc = S.config_scene("c2")
     cams = S.config_cameras("c2")
     foam = foam_of(sc)
-    out = foam.render(cams, record=384)
-    _both(foam, cams, out, torch.randn_like(out["rgb"]) * 1e-3, SAME_FULL)
+    errs = _check_backward_sampled(sc, foam, cams, record=RECORD, shared_cells=True)
+    print("c2 shared-cell grads vs oracle", errs)
+    for k, e in errs.items():
+        assert e <= GRAD_REL, (k, e)
+    out = foam.render(cams, record=RECORD)
+    gr = torch.randn_like(out["rgb"]) * 1e-3
+    a = foam.backward(cams, out, gr)
+    b = foam.backward(cams, out, gr, shared_cells=True)
+    torch.cuda.synchronize()
+    for k in ("density", "sh"):
+        e = rel_l2(b[k].cpu().numpy(), a[k].cpu().numpy())
+        print(f"{k} rel {e:.1e}")
+        assert e <= SAME_FULL, (k, e)
