@@ -630,7 +630,7 @@ class _scene_as_rendered:
 
 class _Render(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, foam, cams, eps, max_steps, quantile, effects, record, density, sh, pos):
+    def forward(ctx, foam, cams, eps, max_steps, quantile, effects, record, shared_cells, density, sh, pos):
         foam._sync_positions(pos)
         out = foam.render(cams, eps=eps, max_steps=max_steps, quantile=quantile, effects=effects,
                           record=record)
@@ -638,6 +638,7 @@ class _Render(torch.autograd.Function):
         ctx.foam_state = foam.state()
         ctx.foam, ctx.cams, ctx.eps, ctx.max_steps, ctx.quantile = foam, cams, eps, max_steps, quantile
         ctx.effects = effects
+        ctx.shared_cells = shared_cells
         ctx.dtypes = (density.dtype, sh.dtype)
         if quantile:
             ctx.save_for_backward(out["rgb"], out["trans"], out["depth"], out["quantile_aux"])
@@ -653,11 +654,11 @@ class _Render(torch.autograd.Function):
         need = ctx.needs_input_grad
         dev = rgb.device
         grads = {}
-        if need[7]:
-            grads["density"] = torch.zeros(foam.n_sites, device=dev)
         if need[8]:
-            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+            grads["density"] = torch.zeros(foam.n_sites, device=dev)
         if need[9]:
+            grads["sh"] = torch.zeros(tuple(foam.sh.shape), device=dev)
+        if need[10]:
             grads["pos"] = torch.zeros(foam.n_sites, 3, device=dev)
         if grads:
             z = lambda g: None if g is None else g.contiguous().float()
@@ -671,18 +672,19 @@ class _Render(torch.autograd.Function):
                               z(g_rgb) if g_rgb is not None else torch.zeros_like(rgb),
                               z(g_trans), z(g_depth), grads=grads, eps=ctx.eps,
                               max_steps=ctx.max_steps, d_quantile=z(g_quant) if ctx.quantile else None,
-                              effects=ctx.effects)
+                              effects=ctx.effects, shared_cells=ctx.shared_cells)
         gd = grads.get("density")
         gs = grads.get("sh")
         ctx.walk_record = None
-        return (None, None, None, None, None, None, None,
+        return (None, None, None, None, None, None, None, None,
                 None if gd is None else gd.to(ctx.dtypes[0]),
                 None if gs is None else gs.to(ctx.dtypes[1]),
                 grads.get("pos"))
 
 
 def render(foam: Foam, cams, density=None, sh=None, pos=None, eps: float = 1e-4,
-           max_steps: int = 0, quantile: bool = False, effects=None, record: int = 256):
+           max_steps: int = 0, quantile: bool = False, effects=None, record: int = 256,
+           shared_cells: bool = False):
     """Differentiable render of ``cams``: returns (rgb [R,3], trans [R],
     depth [R]) and, with ``quantile``, the per-ray quantile loss of Eq. (6)
     [R]; gradients flow to ``density``, ``sh`` and ``pos`` (defaults: the
@@ -690,11 +692,14 @@ def render(foam: Foam, cams, density=None, sh=None, pos=None, eps: float = 1e-4,
     steps per ray of the segment record kept between the passes, 24 bytes per
     step for every ray slot of the cameras' 16x8 tiles (12.7 GB for a
     1920x1080 frame at 256 steps); 0: none, the backward then searches every
-    step's exit again and re-reads the attributes."""
+    step's exit again and re-reads the attributes.  ``shared_cells``: the
+    backward for frames whose rays share cells heavily
+    (``RF_RENDER_SHARED_CELLS``)."""
     density = foam.density if density is None else density
     sh = foam.sh if sh is None else sh
     if density is not foam.density or sh is not foam.sh:
         foam.set_attributes(density.detach(), sh.detach())
     if pos is None:
         pos = foam.pos
-    return _Render.apply(foam, cams, eps, max_steps, bool(quantile), effects, int(record), density, sh, pos)
+    return _Render.apply(foam, cams, eps, max_steps, bool(quantile), effects, int(record), bool(shared_cells),
+                         density, sh, pos)

@@ -71,6 +71,25 @@ def test_shared_cells_matches_oracle():
         assert e <= GRAD_REL, (k, e)
 
 
+def test_autograd_shared_cells():
+    sc = random_scene(300, 2, 17)
+    foam = foam_of(sc)
+    cam = camera_at((0.1, 0.1, 0.1), (0.0, 1.0, 0.0), w=32, h=24)
+    res = []
+    for shared in (False, True):
+        dens = foam.density.clone().requires_grad_(True)
+        sh = foam.sh.clone().requires_grad_(True)
+        pos = foam.pos.clone().requires_grad_(True)
+        rgb, tr, dp = rf.render(foam, [cam], dens, sh, pos, shared_cells=shared)
+        (rgb.sum() + 0.5 * tr.sum() + 0.1 * dp.sum()).backward()
+        res.append((dens.grad, sh.grad, pos.grad))
+    for a, b, k in zip(res[0], res[1], ("density", "sh", "pos")):
+        assert a is not None and b is not None, k
+        e = rel_l2(b.cpu().numpy(), a.cpu().numpy())
+        print(f"autograd {k} rel {e:.1e}")
+        assert e <= SAME, (k, e)
+
+
 def test_unknown_flag_bits_are_rejected():
     sc = random_scene(200, 0, 3)
     foam = foam_of(sc)
